@@ -1,0 +1,274 @@
+/*
+ * rsdft.h -- C ABI of the GB300-native real-space Kohn-Sham LOBPCG path.
+ *
+ * The method is the SCF iteration of Ito's QUMASUN paper (arXiv 2512.04447):
+ * per iteration, (1) the FFT Laplacian on all orbitals at once, (2) GEMMs that
+ * form the subspace matrices H and S in LOBPCG, (3) the generalised Hermitian
+ * eigenproblem reduced by a Cholesky factorisation and two triangular solves
+ * (Eq. 1), and (4) the Kleinman-Bylander nonlocal operator, plus the density
+ * and potential updates ("Others", Fig. 1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Cell: orthorhombic, edges (Lx, Ly, Lz) bohr.  Grid (Nx, Ny, Nz), each
+ *    N 5-smooth (2^a 3^b 5^c) with 2 <= N <= 128 (RSDFT_E_GRID_NOT_5SMOOTH
+ *    otherwise).  Point r = (ix Lx/Nx, iy Ly/Ny, iz Lz/Nz); linear index
+ *    i = (iz*Ny + iy)*Nx + ix (x fastest); n = Nx*Ny*Nz; dV = Lx*Ly*Lz/n.
+ *  - Orbital blocks: [nband][n] complex128 (interleaved re, im), band-major.
+ *    Inner product <a|b> = sum_r conj(a(r)) b(r) dV; orbitals are
+ *    normalised in that metric.
+ *  - Kinetic operator: T psi = IFFT(|G|^2/2 FFT(psi)), G = 2 pi k / L with k
+ *    in FFT order (0..N/2-1, -N/2..-1).
+ *  - Nonlocal operator: sum_{a,j} |beta_aj> E_aj <beta_aj|psi>, with
+ *    projectors s, p_x, p_y, p_z = (1, d_x/rc, d_y/rc, d_z/rc) exp(-|d|^2/(2 rc^2)),
+ *    d the minimal-image displacement from atom a, truncated to |d| < rcut and
+ *    normalised on the grid (sum beta^2 dV = 1).
+ *  - Pointers named *_dev are device memory owned by the caller; *_host are
+ *    host memory owned by the caller.  Nothing is retained after a call
+ *    returns except by rsdft_create (which copies its inputs).
+ *  - Every call returns an rsdft_status.  No call aborts or throws.  On
+ *    failure rsdft_last_error(ctx) describes it; caller-owned outputs are left
+ *    in their last valid state.  A context is used by one host thread at a
+ *    time; work is issued on the CUDA stream passed in (NULL = legacy stream),
+ *    and calls that return host values synchronise that stream first.
+ */
+#ifndef RSDFT_H
+#define RSDFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsdft_ctx rsdft_ctx;
+
+typedef enum {
+    RSDFT_OK = 0,
+    RSDFT_E_INVALID = 1,           /* bad argument (null, size, range)            */
+    RSDFT_E_GRID_NOT_5SMOOTH = 2,  /* a grid dimension is not 2^a 3^b 5^c <= 128  */
+    RSDFT_E_OOM = 3,               /* device allocation failed                    */
+    RSDFT_E_CUDA = 4,              /* a CUDA runtime call or launch failed        */
+    RSDFT_E_NOT_SPD = 5,           /* overlap matrix has fewer independent columns
+                                      than wanted eigenpairs                       */
+    RSDFT_E_NUMERIC = 6,           /* NaN/Inf met in residuals or energies        */
+    RSDFT_E_TIMEOUT = 7,           /* reserved: a bounded device wait gave up     */
+    RSDFT_E_NOT_CONVERGED = 8      /* informational: outputs valid, tol not met   */
+} rsdft_status;
+
+typedef enum { RSDFT_FP64 = 0, RSDFT_MIXED = 1 } rsdft_precision;
+typedef enum { RSDFT_PRECOND_NONE = 0, RSDFT_PRECOND_TPA = 1 } rsdft_precond;
+
+/* Lattice vectors as rows, bohr.  Only diagonal (orthorhombic) cells are
+ * accepted; off-diagonal entries must be 0 (RSDFT_E_INVALID otherwise). */
+typedef struct { double a[3][3]; } rsdft_cell;
+
+/* Grid points along x, y, z. */
+typedef struct { int n[3]; } rsdft_grid;
+
+/* Gaussian KB projectors (the synthetic pseudo-atoms of the workloads). */
+typedef struct {
+    int natom;             /* >= 0                                               */
+    const double *pos;     /* [natom][3] bohr, host                              */
+    int nproj;             /* 1 (s) or 4 (s, p_x, p_y, p_z)                      */
+    double rc;             /* Gaussian radius, bohr, > 0                         */
+    double rcut;           /* truncation radius, 0 < rcut < min(L)/2             */
+    const double *e_kb;    /* [natom][nproj] KB energies, Ha, host               */
+} rsdft_projectors;
+
+/* ---------------------------------------------------------------------------
+ * Context: grid, FFT tables, local potential, projector tables, device arena.
+ * Follows the paper's statement of the problem (H = T + V + V_NL on a
+ * real-space grid).  v_loc_host: [n] local potential, Ha, copied.  proj may be
+ * NULL (no nonlocal term).  On success *out owns all device memory it uses;
+ * release it with rsdft_destroy.
+ */
+rsdft_status rsdft_create(const rsdft_cell *cell, const rsdft_grid *grid,
+                          const double *v_loc_host, const rsdft_projectors *proj,
+                          rsdft_ctx **out);
+void rsdft_destroy(rsdft_ctx *ctx);
+
+/* Text of the last error on ctx (or of the last failed rsdft_create on this
+ * thread when ctx is NULL).  Valid until the next call on the same ctx. */
+const char *rsdft_last_error(const rsdft_ctx *ctx);
+
+/* Input builder for the synthetic workloads: V(r) = sum_a -Z exp(-|d_a|^2 /
+ * (2 sigma^2)), minimal-image d_a.  Host only; out_host is [n] doubles. */
+rsdft_status rsdft_gaussian_vloc(const rsdft_cell *cell, const rsdft_grid *grid, int natom,
+                                 const double *pos_host, double Z, double sigma,
+                                 double *out_host);
+
+/* Replace the local potential V(r) used by H (e.g. V_loc + V_H + V_xc).
+ * v: [n] doubles, on the device when on_device != 0, else on the host. */
+rsdft_status rsdft_set_potential(rsdft_ctx *ctx, const double *v, int on_device, void *stream);
+
+/* Number of projector table entries (points inside all spheres, summed over
+ * atoms), for sizing and roofline accounting. */
+long long rsdft_projector_entries(const rsdft_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * H psi for a block of orbitals (SCF tasks (1) and (4)): batched 3D FFT
+ * kinetic term with the local-potential product and the projector scatter
+ * fused into the last pass.  psi_dev, hpsi_dev: [nband][n] complex128
+ * (RSDFT_FP64) or complex64 (RSDFT_MIXED); must not overlap.  nband >= 0.
+ */
+rsdft_status rsdft_apply_h(rsdft_ctx *ctx, const void *psi_dev, void *hpsi_dev, int nband,
+                           rsdft_precision prec, void *stream);
+
+/* Projector coefficients p[b][a*nproj + j] = <beta_aj|psi_b> (complex128).
+ * psi_dev: [nband][n] complex128; p_dev: [nband][natom*nproj] complex128. */
+rsdft_status rsdft_project(rsdft_ctx *ctx, const void *psi_dev, void *p_dev, int nband,
+                           void *stream);
+
+/* Teter-Payne-Allan preconditioner: w_b = IFFT(K(|G|^2/2 / t_b) FFT(r_b)),
+ * K(x) = (27+18x+12x^2+8x^3)/(27+18x+12x^2+8x^3+16x^4); t_b < 1e-12 is
+ * replaced by 1.  r_dev, w_dev: [nband][n] complex128 (may alias);
+ * tkin_dev: [nband] doubles. */
+rsdft_status rsdft_precondition_tpa(rsdft_ctx *ctx, const void *r_dev, void *w_dev,
+                                    const double *tkin_dev, int nband, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Subspace building blocks of the LOBPCG iteration (SCF tasks (2)-(3)).
+ *
+ * Gram matrix G[i][j] = <a_i|b_j> = dV sum_r conj(a_i(r)) b_j(r).
+ * a_dev: [na][n], b_dev: [nb][n], g_dev: [na][nb] row-major, complex128.
+ */
+rsdft_status rsdft_gram(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
+                        void *g_dev, void *stream);
+
+/* Rotation out[b] = sum_i c[i][b] y[i] (+ base[b] when base_dev != NULL;
+ * base may alias out).  y_dev: [k][n]; c_dev: [k][m] row-major;
+ * out_dev, base_dev: [m][n]; complex128.  sign = +1 adds, -1 subtracts the sum. */
+rsdft_status rsdft_rotate(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
+                          const void *base_dev, int sign, void *out_dev, void *stream);
+
+/* Rayleigh-Ritz of Eq. 1 on a k x k Hermitian pair (row-major complex128 on
+ * the device; inputs are not modified): G_S = L L^H (columns whose pivot
+ * falls to pivot_tol * max diag are dropped), K = L^-1 G_H L^-H by two
+ * triangular solves, K Z = Z Lambda for the lowest nkeep, C = L^-H Z.
+ * lam_host: [nkeep] ascending; c_dev: [k][nkeep] (zero rows for dropped
+ * columns); *ndropped_host: columns dropped.  RSDFT_E_NOT_SPD if fewer than
+ * nkeep columns are independent. */
+rsdft_status rsdft_rayleigh_ritz(rsdft_ctx *ctx, const void *gh_dev, const void *gs_dev, int k,
+                                 int nkeep, double pivot_tol, double *lam_host, void *c_dev,
+                                 int *ndropped_host, void *stream);
+
+/* Subspace Hermitian eigensolve alone: the lowest nkeep eigenpairs of a k x k
+ * Hermitian matrix (row-major complex128, device, not modified).
+ * lam_host: [nkeep]; z_dev: [k][nkeep] orthonormal columns. */
+rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, double *lam_host,
+                        void *z_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * LOBPCG for the lowest nband eigenpairs of H (the paper's eigensolver,
+ * Knyazev's block method with the Rayleigh-Ritz of Eq. 1).
+ * x_dev: in/out [nband][n] complex128 (initial guess in, Ritz vectors out,
+ * orthonormal).  eig_host, resnorm_host: [nband].
+ */
+typedef struct {
+    int maxit;             /* iterations cap (>= 0)                                */
+    double tol;            /* stop when max residual over the first nconv <= tol   */
+    int nconv;             /* bands checked for tol; <= 0 means nband              */
+    int precond;           /* rsdft_precond                                        */
+    int precision;         /* rsdft_precision (RSDFT_FP64 only in this version)    */
+    double lock_tol;       /* soft-lock bands with residual <= lock_tol (1e-10)    */
+    double pivot_tol;      /* relative Cholesky pivot floor for G_S (1e-8)         */
+} rsdft_lobpcg_opts;
+
+typedef struct {
+    int iterations;        /* full iterations done                                 */
+    int converged;         /* 1 if the tolerance test passed                       */
+    int dropped;           /* basis columns dropped by the Cholesky, summed        */
+    double ms_hpsi, ms_precond, ms_gram, ms_dense, ms_rotate, ms_other;
+} rsdft_lobpcg_stats;
+
+void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *opts);
+
+rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
+                          double *eig_host, double *resnorm_host, rsdft_lobpcg_stats *stats,
+                          void *stream);
+
+/* ---------------------------------------------------------------------------
+ * SCF step: V_eff = V_loc + V_H[rho_in] + v_xc[rho_in] (FFT Hartree, LDA
+ * Slater + Perdew-Zunger 1981), LOBPCG (converged on the first step, k_lobpcg
+ * iterations afterwards), occupations (aufbau, or Fermi-Dirac at kT > 0),
+ * rho_out = sum f |psi|^2, energies, Anderson mixing of rho_in.  The density
+ * and the mixing history live in the context (rsdft_scf_init resets them to
+ * the uniform density N_e / volume).
+ */
+typedef struct {
+    double n_electrons;    /* spin-degenerate electron count (> 0)                 */
+    double kT;             /* Ha; 0 = aufbau                                       */
+    double beta;           /* Anderson weight (0.3)                                */
+    int depth;             /* Anderson history depth (4)                           */
+    int k_lobpcg;          /* LOBPCG iterations per step after the first (3)       */
+    int first_maxit;       /* iteration cap of the first, converged, solve (200)   */
+    double tol;            /* residual tolerance of the first solve (1e-6)         */
+    int precond;           /* rsdft_precond                                        */
+} rsdft_scf_opts;
+
+typedef struct {
+    double e_tot;          /* sum f eps - E_H - int v_xc rho + E_xc (at rho_in)    */
+    double free_energy;    /* e_tot - kT S                                         */
+    double e_band, e_h, e_xc, e_vxc, mu, entropy;
+    double drho;           /* ||rho_out - rho_in|| sqrt(dV)                        */
+    int lobpcg_iterations;
+    int step;              /* index of the step just done (0-based)                */
+} rsdft_scf_out;
+
+void rsdft_scf_default_opts(rsdft_scf_opts *opts);
+rsdft_status rsdft_scf_init(rsdft_ctx *ctx, int nband, const rsdft_scf_opts *opts, void *stream);
+/* eig_host, occ_host: [nband] outputs (may be NULL). */
+rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
+                            rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream);
+
+/* SCF field pieces, each on [n] doubles on the device:
+ * rho = sum_b f_b |x_b|^2 (x_dev [nband][n] complex128, f_dev [nband]);
+ * V_H by FFT Poisson (G = 0 term removed);
+ * LDA eps_xc and v_xc (rho < 1e-12 gives 0). */
+rsdft_status rsdft_density(rsdft_ctx *ctx, const void *x_dev, const double *f_dev, int nband,
+                           double *rho_dev, void *stream);
+rsdft_status rsdft_hartree(rsdft_ctx *ctx, const double *rho_dev, double *vh_dev, void *stream);
+rsdft_status rsdft_lda(rsdft_ctx *ctx, const double *rho_dev, double *eps_dev, double *vxc_dev,
+                       void *stream);
+/* Occupations on the device: eig_dev [nband] ascending -> f_dev [nband];
+ * mu_host, entropy_host may be NULL. */
+rsdft_status rsdft_occupations(rsdft_ctx *ctx, const double *eig_dev, int nband,
+                               double n_electrons, double kT, double *f_dev, double *mu_host,
+                               double *entropy_host, void *stream);
+/* Density rho_in as held by the SCF state (device, [n]); NULL before init. */
+const double *rsdft_scf_density(const rsdft_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Per-kernel timing (the per-component breakdown of Fig. 1, finer grained).
+ * When enabled, each launch of the hot kernels below is bracketed by CUDA
+ * events on its stream and its algorithmic work is recorded: flops counted
+ * from the operation's definition (complex MAC = 8, FFT = 5 N log2 N per
+ * transform) and bytes = the minimum HBM traffic of the operation (each
+ * operand read once, each result written once).  Reading synchronises the
+ * events.  Enabling resets the counters.
+ */
+typedef enum {
+    RSDFT_K_GRAM = 0,        /* Gram partial tiles (split-K)                    */
+    RSDFT_K_ROTATE = 1,      /* Ritz rotation / block update                    */
+    RSDFT_K_FFT_XY_FWD = 2,  /* xy-plane forward FFT pass                       */
+    RSDFT_K_FFT_Z = 3,       /* z pass: forward, per-G factor, inverse          */
+    RSDFT_K_FFT_XY_INV = 4,  /* xy-plane inverse pass (+ V psi + projectors)    */
+    RSDFT_K_PROJECT = 5,     /* projector gather <beta|psi>                     */
+    RSDFT_K_DENSE = 6,       /* Cholesky, TRSM, eigensolve of the subspace      */
+    RSDFT_K_COUNT = 7
+} rsdft_kernel_id;
+
+rsdft_status rsdft_profile_enable(rsdft_ctx *ctx, int on);
+/* Totals since enabling for one kernel id: summed event time (ms), launches,
+ * algorithmic flops and bytes.  Any pointer may be NULL. */
+rsdft_status rsdft_profile_read(rsdft_ctx *ctx, int kernel_id, double *ms, long long *launches,
+                                double *flops, double *bytes);
+/* Kernels launched on ctx since creation (every kernel, profiled or not). */
+long long rsdft_launch_count(const rsdft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSDFT_H */

@@ -75,7 +75,11 @@ def tpa_factor(x: np.ndarray) -> np.ndarray:
 
 def tpa_precondition(ham: Hamiltonian, R: np.ndarray, X: np.ndarray) -> np.ndarray:
     """W_b = IFFT(K((|G|^2/2)/T_b) FFT(R_b)), T_b = <x_b|T|x_b>."""
-    tb = ham.kinetic_energy(X)
+    return tpa_apply(ham, R, ham.kinetic_energy(X))
+
+
+def tpa_apply(ham: Hamiltonian, R: np.ndarray, tb: np.ndarray) -> np.ndarray:
+    """W_b = IFFT(K((|G|^2/2)/t_b) FFT(R_b)) for given t_b (< 1e-12 -> 1)."""
     tb = np.where(tb < 1e-12, 1.0, tb)
     m = R.shape[0]
     shape = ham.grid.shape

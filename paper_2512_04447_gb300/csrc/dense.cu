@@ -1,0 +1,756 @@
+// Dense core of the Rayleigh-Ritz step (SCF task (3), Eq. 1), FP64 complex,
+// all on the device:
+//   Cholesky G_S = L L^H (blocked, right-looking; a column whose pivot falls to
+//   the floor is dropped), compaction to the kept columns, two triangular
+//   solves K = L^-1 G_H L^-H, the lowest eigenpairs of K (Householder
+//   tridiagonalisation, Sturm bisection, inverse iteration, Gram-Schmidt within
+//   eigenvalue clusters, back-transformation), and C = L^-H Z.
+// Matrices are row-major k x k complex128 with leading dimension ld.
+#include <cfloat>
+#include <cmath>
+
+#include "rsdft_internal.h"
+
+namespace rsdft {
+
+constexpr int NBK = 32;   // block size of the Cholesky and the triangular solves
+
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 c_mulc(double2 a, double2 b) {  // a * conj(b)
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 c_conj(double2 a) { return make_double2(a.x, -a.y); }
+
+// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024).
+__device__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        sh[32] = s;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// ---- Cholesky with dropping -----------------------------------------------------
+__global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double tol, double *out) {
+    __shared__ double sh[33];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) m = fmax(m, a[(size_t)i * ld + i].x);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+        out[0] = tol * r;
+    }
+}
+
+// Factor columns kb..kb+nb-1 (rows kb..k-1), in place in the lower triangle.
+__global__ void k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp,
+                             int *drop) {
+    const double floor_ = floorp[0];
+    __shared__ double s_l;
+    __shared__ int s_drop;
+    for (int c = kb; c < kb + nb; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = a[(size_t)c * ld + c].x;
+            s_drop = !(d > floor_);
+            s_l = s_drop ? 1.0 : sqrt(d);
+            drop[c] = s_drop;
+            a[(size_t)c * ld + c] = make_double2(s_l, 0.0);
+        }
+        __syncthreads();
+        const double inv = 1.0 / s_l;
+        for (int i = c + 1 + threadIdx.x; i < k; i += blockDim.x) {
+            double2 &x = a[(size_t)i * ld + c];
+            x = s_drop ? make_double2(0.0, 0.0) : make_double2(x.x * inv, x.y * inv);
+        }
+        __syncthreads();
+        if (!s_drop) {
+            // remaining columns of the panel: a[i][c2] -= l[i][c] conj(l[c2][c]), i >= c2
+            const int ncol = kb + nb - (c + 1);
+            const int nrow = k - (c + 1);
+            for (int t = threadIdx.x; t < ncol * nrow; t += blockDim.x) {
+                const int cc = c + 1 + t / nrow;
+                const int i = c + 1 + t % nrow;
+                if (i < cc) continue;
+                const double2 li = a[(size_t)i * ld + c];
+                const double2 lc = a[(size_t)cc * ld + c];
+                double2 &x = a[(size_t)i * ld + cc];
+                const double2 p = c_mulc(li, lc);
+                x.x -= p.x;
+                x.y -= p.y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb.
+__global__ void k_chol_update(double2 *a, int k, int ld, int kb, int nb) {
+    const int t0 = kb + nb;
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    const int i0 = t0 + ti * 32, j0 = t0 + tj * 32;
+    __shared__ double2 Li[32][NBK + 1], Lj[32][NBK + 1];
+    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        Li[r][c] = (i0 + r < k) ? a[(size_t)(i0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
+        Lj[r][c] = (j0 + r < k) ? a[(size_t)(j0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int r = t / 32, s = t % 32;
+        const int i = i0 + r, j = j0 + s;
+        if (i >= k || j >= k || j > i) continue;
+        double sx = 0.0, sy = 0.0;
+        for (int c = 0; c < nb; ++c) {
+            const double2 p = c_mulc(Li[r][c], Lj[s][c]);
+            sx += p.x;
+            sy += p.y;
+        }
+        double2 &x = a[(size_t)i * ld + j];
+        x.x -= sx;
+        x.y -= sy;
+    }
+}
+
+__global__ void k_keep_scan(const int *drop, int k, int *keep) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 0;
+    for (int i = 0; i < k; ++i)
+        if (!drop[i]) keep[c++] = i;
+    keep[k] = c;
+}
+
+// out[r][s] = in[keep[r]][keep[s]] for r, s < kc.
+__global__ void k_gather_sq(const double2 *__restrict__ in, int ldi, const int *__restrict__ keep,
+                            int kc, double2 *__restrict__ out, int ldo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kc * kc) return;
+    const int r = (int)(idx / kc), s = (int)(idx % kc);
+    out[(size_t)r * ldo + s] = in[(size_t)keep[r] * ldi + keep[s]];
+}
+
+// out = (in^H), kc x kc
+__global__ void k_conj_transpose(const double2 *__restrict__ in, int ldi, int kc,
+                                 double2 *__restrict__ out, int ldo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kc * kc) return;
+    const int r = (int)(idx / kc), s = (int)(idx % kc);
+    out[(size_t)r * ldo + s] = c_conj(in[(size_t)s * ldi + r]);
+}
+
+// out = (a + a^H) / 2, kc x kc (out may not alias a)
+__global__ void k_hermitise(const double2 *__restrict__ a, int lda, int kc, double2 *__restrict__ out,
+                            int ldo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kc * kc) return;
+    const int r = (int)(idx / kc), s = (int)(idx % kc);
+    const double2 x = a[(size_t)r * lda + s], y = a[(size_t)s * lda + r];
+    out[(size_t)r * ldo + s] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+}
+
+// ---- triangular solves with the lower factor L (kc x kc) ----------------------------
+// Forward: solve L X = B in place (B: kc x ncol, ld ldb), one block row at a time.
+__global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
+                                  double2 *b, int ldb, int ncol) {
+    __shared__ double2 Ls[NBK][NBK + 1];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
+    }
+    __syncthreads();
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    double2 x[NBK];
+    for (int r = 0; r < nb; ++r) {
+        double2 v = b[(size_t)(rb + r) * ldb + col];
+        for (int c = 0; c < r; ++c) {
+            const double2 p = c_mul(Ls[r][c], x[c]);
+            v.x -= p.x;
+            v.y -= p.y;
+        }
+        const double inv = 1.0 / Ls[r][r].x;  // real positive diagonal
+        x[r] = make_double2(v.x * inv, v.y * inv);
+    }
+    for (int r = 0; r < nb; ++r) b[(size_t)(rb + r) * ldb + col] = x[r];
+}
+
+// b[i][col] -= sum_{c<nb} L[i][rb+c] b[rb+c][col] for i in [rb+nb, kc)
+__global__ void k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int kc, int rb, int nb,
+                                    double2 *b, int ldb, int ncol) {
+    const int i0 = rb + nb + blockIdx.y * 32, c0 = blockIdx.x * 32;
+    __shared__ double2 Ls[32][NBK + 1], Xs[NBK][33];
+    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        Ls[r][c] = (i0 + r < kc) ? L[(size_t)(i0 + r) * ldl + rb + c] : make_double2(0.0, 0.0);
+        const int xr = t / 32, xc = t % 32;
+        Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int r = t / 32, s = t % 32;
+        const int i = i0 + r, col = c0 + s;
+        if (i >= kc || col >= ncol) continue;
+        double sx = 0.0, sy = 0.0;
+        for (int c = 0; c < nb; ++c) {
+            const double2 p = c_mul(Ls[r][c], Xs[c][s]);
+            sx += p.x;
+            sy += p.y;
+        }
+        double2 &x = b[(size_t)i * ldb + col];
+        x.x -= sx;
+        x.y -= sy;
+    }
+}
+
+// Backward: solve L^H X = B in place, block rows from the bottom.
+__global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
+                                   double2 *b, int ldb, int ncol) {
+    __shared__ double2 Ls[NBK][NBK + 1];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
+    }
+    __syncthreads();
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    double2 x[NBK];
+    for (int r = nb - 1; r >= 0; --r) {
+        double2 v = b[(size_t)(rb + r) * ldb + col];
+        for (int c = r + 1; c < nb; ++c) {
+            // (L^H)[r][c] = conj(L[c][r])
+            const double2 p = c_mul(c_conj(Ls[c][r]), x[c]);
+            v.x -= p.x;
+            v.y -= p.y;
+        }
+        const double inv = 1.0 / Ls[r][r].x;
+        x[r] = make_double2(v.x * inv, v.y * inv);
+    }
+    for (int r = 0; r < nb; ++r) b[(size_t)(rb + r) * ldb + col] = x[r];
+}
+
+// b[i][col] -= sum_{c<nb} conj(L[rb+c][i]) b[rb+c][col] for i in [0, rb)
+__global__ void k_trsm_upperH_update(const double2 *__restrict__ L, int ldl, int rb, int nb,
+                                     double2 *b, int ldb, int ncol) {
+    const int i0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    __shared__ double2 Ls[32][NBK + 1], Xs[NBK][33];
+    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        Ls[r][c] = (i0 + r < rb) ? c_conj(L[(size_t)(rb + c) * ldl + i0 + r]) : make_double2(0.0, 0.0);
+        const int xr = t / 32, xc = t % 32;
+        Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int r = t / 32, s = t % 32;
+        const int i = i0 + r, col = c0 + s;
+        if (i >= rb || col >= ncol) continue;
+        double sx = 0.0, sy = 0.0;
+        for (int c = 0; c < nb; ++c) {
+            const double2 p = c_mul(Ls[r][c], Xs[c][s]);
+            sx += p.x;
+            sy += p.y;
+        }
+        double2 &x = b[(size_t)i * ldb + col];
+        x.x -= sx;
+        x.y -= sy;
+    }
+}
+
+static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
+                               int ldb, int ncol, cudaStream_t st) {
+    for (int rb = 0; rb < kc; rb += NBK) {
+        const int nb = std::min(NBK, kc - rb);
+        k_trsm_lower_diag<<<cdiv(ncol, 64), 64, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        count_launch(ctx);
+        const int rest = kc - rb - nb;
+        if (rest > 0) {
+            dim3 g(cdiv(ncol, 32), cdiv(rest, 32));
+            k_trsm_lower_update<<<g, 256, 0, st>>>(L, ldl, kc, rb, nb, b, ldb, ncol);
+            count_launch(ctx);
+        }
+    }
+    RS_LAUNCHED(ctx, "trsm_lower");
+    return RSDFT_OK;
+}
+
+static rsdft_status trsm_upperH(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
+                                int ldb, int ncol, cudaStream_t st) {
+    const int nblk = cdiv(kc, NBK);
+    for (int q = nblk - 1; q >= 0; --q) {
+        const int rb = q * NBK;
+        const int nb = std::min(NBK, kc - rb);
+        k_trsm_upperH_diag<<<cdiv(ncol, 64), 64, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        count_launch(ctx);
+        if (rb > 0) {
+            dim3 g(cdiv(ncol, 32), cdiv(rb, 32));
+            k_trsm_upperH_update<<<g, 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+            count_launch(ctx);
+        }
+    }
+    RS_LAUNCHED(ctx, "trsm_upperH");
+    return RSDFT_OK;
+}
+
+// ---- Hermitian eigensolver ----------------------------------------------------------
+// Householder step i (LAPACK zhetd2 convention, lower): reflector H = I - tau v v^H
+// with v[0] = 1 such that H^H (alpha, x)^T = (beta, 0)^T, beta real.
+__global__ void k_house_reflector(double2 *a, int k, int ld, int i, double2 *vh, int ldv,
+                                  double2 *tau, double *d, double *e) {
+    __shared__ double sh[33];
+    const int L = k - i - 1;
+    const double2 alpha = a[(size_t)(i + 1) * ld + i];
+    double s = 0.0;
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) {
+        const double2 x = a[(size_t)(i + 1 + r) * ld + i];
+        s += x.x * x.x + x.y * x.y;
+    }
+    const double xnorm2 = block_sum(s, sh);
+    double2 t;
+    double beta;
+    double2 scal = make_double2(0.0, 0.0);
+    if (xnorm2 == 0.0 && alpha.y == 0.0) {
+        t = make_double2(0.0, 0.0);
+        beta = alpha.x;
+    } else {
+        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
+        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        // scal = 1 / (alpha - beta)
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double dd = den.x * den.x + den.y * den.y;
+        scal = make_double2(den.x / dd, -den.y / dd);
+    }
+    double2 *v = vh + (size_t)i * ldv + (i + 1);
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        if (r == 0) v[0] = make_double2(1.0, 0.0);
+        else v[r] = c_mul(a[(size_t)(i + 1 + r) * ld + i], scal);
+    }
+    if (threadIdx.x == 0) {
+        tau[i] = t;
+        e[i] = beta;
+        d[i] = a[(size_t)i * ld + i].x;
+    }
+}
+
+// w[r] = tau * sum_c A22[r][c] v[c]; one warp per row.
+__global__ void k_house_matvec(const double2 *__restrict__ a, int k, int ld, int i,
+                               const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tau,
+                               double2 *__restrict__ w) {
+    const int L = k - i - 1;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= L) return;
+    const double2 *row = a + (size_t)(i + 1 + warp) * ld + (i + 1);
+    const double2 *v = vh + (size_t)i * ldv + (i + 1);
+    double sx = 0.0, sy = 0.0;
+    for (int c = lane; c < L; c += 32) {
+        const double2 p = c_mul(row[c], v[c]);
+        sx += p.x;
+        sy += p.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) w[warp] = c_mul(tau[i], make_double2(sx, sy));
+}
+
+// alpha = -1/2 tau (w^H v); w += alpha v
+__global__ void k_house_w(int k, int i, const double2 *__restrict__ vh, int ldv,
+                          const double2 *__restrict__ tau, double2 *w) {
+    __shared__ double sh[33];
+    const int L = k - i - 1;
+    const double2 *v = vh + (size_t)i * ldv + (i + 1);
+    double sx = 0.0, sy = 0.0;
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        const double2 p = c_mul(c_conj(w[r]), v[r]);
+        sx += p.x;
+        sy += p.y;
+    }
+    sx = block_sum(sx, sh);
+    sy = block_sum(sy, sh);
+    const double2 tw = c_mul(tau[i], make_double2(sx, sy));
+    const double2 alpha = make_double2(-0.5 * tw.x, -0.5 * tw.y);
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        const double2 p = c_mul(alpha, v[r]);
+        w[r].x += p.x;
+        w[r].y += p.y;
+    }
+}
+
+// A22 -= v w^H + w v^H
+__global__ void k_house_rank2(double2 *a, int k, int ld, int i, const double2 *__restrict__ vh, int ldv,
+                              const double2 *__restrict__ w) {
+    const int L = k - i - 1;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (c >= L || r >= L) return;
+    const double2 *v = vh + (size_t)i * ldv + (i + 1);
+    const double2 p = c_mulc(v[r], w[c]);
+    const double2 q = c_mulc(w[r], v[c]);
+    double2 &x = a[(size_t)(i + 1 + r) * ld + (i + 1 + c)];
+    x.x -= p.x + q.x;
+    x.y -= p.y + q.y;
+}
+
+__global__ void k_house_last(const double2 *a, int k, int ld, double *d) {
+    d[k - 1] = a[(size_t)(k - 1) * ld + (k - 1)].x;
+}
+
+// Sturm count: number of eigenvalues of T below x.
+__device__ int sturm_count(const double *d, const double *e2, int k, double x, double pivmin) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+    for (int i = 1; i < k; ++i) {
+        q = d[i] - x - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// scr: [0] tnorm, [1] glo, [2] ghi, [3] pivmin, then e2[k]
+__global__ void k_tri_prep(const double *d, const double *e, int k, double *scr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double *e2 = scr + 8;
+    double tn = 0.0, lo = 1e300, hi = -1e300, emax2 = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double el = i > 0 ? fabs(e[i - 1]) : 0.0;
+        const double er = i < k - 1 ? fabs(e[i]) : 0.0;
+        tn = fmax(tn, fabs(d[i]) + el + er);
+        lo = fmin(lo, d[i] - el - er);
+        hi = fmax(hi, d[i] + el + er);
+        if (i < k - 1) {
+            e2[i] = e[i] * e[i];
+            emax2 = fmax(emax2, e2[i]);
+        }
+    }
+    const double pad = 2.0 * DBL_EPSILON * fmax(tn, 1e-300) + 1e-300;
+    scr[0] = tn;
+    scr[1] = lo - pad;
+    scr[2] = hi + pad;
+    scr[3] = DBL_MIN * fmax(1.0, emax2);
+}
+
+__global__ void k_bisect(const double *d, int k, int nkeep, const double *scr, double *lam) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nkeep) return;
+    const double *e2 = scr + 8;
+    double lo = scr[1], hi = scr[2];
+    const double pivmin = scr[3];
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(d, e2, k, mid, pivmin) > j) hi = mid;
+        else lo = mid;
+    }
+    lam[j] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_uniform(unsigned long long x) {
+    x += 0x9e3779b97f4a7c15ULL;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    x ^= x >> 31;
+    return ((double)(x >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// Inverse iteration for eigenvalue j: three solves of (T - lam_j I) y = x with
+// partial pivoting (row interchanges), normalising after each solve; the
+// start vector is a fixed pseudo-random one.  Vector j goes to zt[j][0..k).
+// fac: per-eigenvalue scratch [nkeep][5][k] (U0, U1, U2, multipliers, swaps).
+__global__ void k_inverse_iter(const double *d, const double *e, int k, int nkeep,
+                               const double *lam, const double *scr, double *fac, double *zt) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nkeep) return;
+    const double tiny = DBL_EPSILON * fmax(scr[0], 1e-300);
+    double *D = fac + (size_t)j * 5 * k;
+    double *U1 = D + k, *U2 = U1 + k, *M = U2 + k, *F = M + k;
+    double *x = zt + (size_t)j * k;
+    const double s = lam[j];
+    for (int i = 0; i < k; ++i) {
+        D[i] = d[i] - s;
+        U1[i] = i < k - 1 ? e[i] : 0.0;
+        U2[i] = 0.0;
+        M[i] = 0.0;
+        F[i] = 0.0;
+    }
+    for (int i = 0; i < k - 1; ++i) {
+        const double sub = e[i];
+        if (fabs(D[i]) >= fabs(sub)) {
+            if (D[i] == 0.0) D[i] = tiny;
+            M[i] = sub / D[i];
+            D[i + 1] -= M[i] * U1[i];
+        } else {
+            // interchange rows i and i+1, then eliminate
+            const double mult = D[i] / sub;
+            const double dk1 = D[i + 1], uk = U1[i], uk1 = U1[i + 1];
+            D[i] = sub;
+            U1[i] = dk1;
+            U2[i] = uk1;
+            D[i + 1] = uk - mult * dk1;
+            U1[i + 1] = -mult * uk1;
+            M[i] = mult;
+            F[i] = 1.0;
+        }
+    }
+    for (int i = 0; i < k; ++i)
+        if (fabs(D[i]) < tiny) D[i] = D[i] < 0.0 ? -tiny : tiny;
+    for (int i = 0; i < k; ++i)
+        x[i] = hash_uniform(((unsigned long long)(j + 1) << 32) + (unsigned long long)i);
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i < k - 1; ++i) {
+            if (F[i] != 0.0) {
+                const double t = x[i];
+                x[i] = x[i + 1];
+                x[i + 1] = t - M[i] * x[i];
+            } else {
+                x[i + 1] -= M[i] * x[i];
+            }
+        }
+        x[k - 1] /= D[k - 1];
+        if (k >= 2) x[k - 2] = (x[k - 2] - U1[k - 2] * x[k - 1]) / D[k - 2];
+        for (int i = k - 3; i >= 0; --i) x[i] = (x[i] - U1[i] * x[i + 1] - U2[i] * x[i + 2]) / D[i];
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = 0; i < k; ++i) x[i] *= nrm;
+    }
+}
+
+// Gram-Schmidt (two passes) of each vector against the earlier vectors of its
+// eigenvalue cluster (consecutive eigenvalues closer than 1e-3 ||T||).
+__global__ void k_cluster_gs(int k, int nkeep, const double *lam, const double *scr, double *zt) {
+    __shared__ double sh[33];
+    __shared__ double dots[1024];
+    const double ortol = 1e-3 * scr[0];
+    int cstart = 0;
+    for (int j = 0; j < nkeep; ++j) {
+        if (j > 0 && !(lam[j] - lam[j - 1] <= ortol)) cstart = j;
+        double *x = zt + (size_t)j * k;
+        for (int pass = 0; pass < 2 && cstart < j; ++pass) {
+            for (int i0 = cstart; i0 < j; i0 += 1024) {
+                const int cnt = min(1024, j - i0);
+                // dots by warps
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                for (int q = warp; q < cnt; q += nw) {
+                    const double *y = zt + (size_t)(i0 + q) * k;
+                    double s = 0.0;
+                    for (int r = lane; r < k; r += 32) s += y[r] * x[r];
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+                    if (lane == 0) dots[q] = s;
+                }
+                __syncthreads();
+                for (int r = threadIdx.x; r < k; r += blockDim.x) {
+                    double v = x[r];
+                    for (int q = 0; q < cnt; ++q) v -= dots[q] * zt[(size_t)(i0 + q) * k + r];
+                    x[r] = v;
+                }
+                __syncthreads();
+            }
+        }
+        double s = 0.0;
+        for (int r = threadIdx.x; r < k; r += blockDim.x) s += x[r] * x[r];
+        s = block_sum(s, sh);
+        const double inv = 1.0 / sqrt(s);
+        for (int r = threadIdx.x; r < k; r += blockDim.x) x[r] *= inv;
+        __syncthreads();
+    }
+}
+
+// z[:, j] = Q zt[j], Q = H(0) H(1) ... H(k-2); one CTA per column.
+__global__ void k_backtransform(int k, const double2 *__restrict__ vh, int ldv,
+                                const double2 *__restrict__ tau, const double *__restrict__ zt,
+                                double2 *z, int ldz) {
+    extern __shared__ double2 sz[];
+    __shared__ double sh[33];
+    const int j = blockIdx.x;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) sz[r] = make_double2(zt[(size_t)j * k + r], 0.0);
+    __syncthreads();
+    for (int i = k - 2; i >= 0; --i) {
+        const double2 t = tau[i];
+        if (t.x == 0.0 && t.y == 0.0) continue;
+        const double2 *v = vh + (size_t)i * ldv;
+        double sx = 0.0, sy = 0.0;
+        for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
+            const double2 p = c_mul(c_conj(v[r]), sz[r]);
+            sx += p.x;
+            sy += p.y;
+        }
+        sx = block_sum(sx, sh);
+        sy = block_sum(sy, sh);
+        const double2 f = c_mul(t, make_double2(sx, sy));
+        for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
+            const double2 p = c_mul(f, v[r]);
+            sz[r].x -= p.x;
+            sz[r].y -= p.y;
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) z[(size_t)r * ldz + j] = sz[r];
+}
+
+rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
+                         double2 *z, int ldz, cudaStream_t st) {
+    Workspace &w = ctx->ws;
+    if (k <= 0 || nkeep <= 0) return RSDFT_OK;
+    if (k > w.cap_k) return fail(ctx, RSDFT_E_INVALID, "subspace %d exceeds workspace %d", k, w.cap_k);
+    if (k == 1) {
+        // 1 x 1: eigenvalue is the real diagonal, eigenvector 1
+        RS_CUDA(ctx, cudaMemcpyAsync(lam_dev, a, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        double2 one = make_double2(1.0, 0.0);
+        RS_CUDA(ctx, cudaMemcpyAsync(z, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
+        return RSDFT_OK;
+    }
+    const int ld = k;
+    for (int i = 0; i < k - 1; ++i) {
+        const int L = k - i - 1;
+        k_house_reflector<<<1, 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.d, w.e);
+        count_launch(ctx);
+        k_house_matvec<<<cdiv((long long)L * 32, 256), 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.wv);
+        count_launch(ctx);
+        k_house_w<<<1, 256, 0, st>>>(k, i, w.Vh, k, w.tau, w.wv);
+        count_launch(ctx);
+        dim3 g(cdiv(L, 128), L);
+        k_house_rank2<<<g, 128, 0, st>>>(a, k, ld, i, w.Vh, k, w.wv);
+        count_launch(ctx);
+    }
+    k_house_last<<<1, 1, 0, st>>>(a, k, ld, w.d);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "householder");
+    k_tri_prep<<<1, 1, 0, st>>>(w.d, w.e, k, w.dscr);
+    count_launch(ctx);
+    k_bisect<<<cdiv(nkeep, 32), 32, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+    count_launch(ctx);
+    k_inverse_iter<<<cdiv(nkeep, 32), 32, 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr, w.fac, w.zt);
+    count_launch(ctx);
+    k_cluster_gs<<<1, 512, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
+    count_launch(ctx);
+    k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "tridiagonal eigensolve");
+    return RSDFT_OK;
+}
+
+__global__ void k_place_rows(const double2 *__restrict__ cc, int kc, int ncol,
+                             const int *__restrict__ keep, double2 *__restrict__ out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kc * ncol) return;
+    const int r = (int)(idx / ncol), c = (int)(idx % ncol);
+    out[(size_t)keep[r] * ncol + c] = cc[idx];
+}
+
+rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,
+                           int nkeep, double pivot_tol, double *lam_dev, double2 *c_out,
+                           int *ndropped, cudaStream_t st) {
+    Workspace &w = ctx->ws;
+    if (k > w.cap_k) return fail(ctx, RSDFT_E_INVALID, "subspace %d exceeds workspace %d", k, w.cap_k);
+    if (nkeep > k || nkeep <= 0) return fail(ctx, RSDFT_E_INVALID, "bad nkeep");
+    const size_t kk = (size_t)k * k;
+    const double kd = (double)k;
+    ProfScope ps(ctx, RSDFT_K_DENSE, 8.0 * kd * kd * kd * (1.0 / 3.0 + 1.0 + 4.0 / 3.0) +
+                 8.0 * kd * kd * nkeep * 1.5, 0.0, st, 0);
+    RS_CUDA(ctx, cudaMemcpyAsync(w.Lm, gs, kk * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    k_maxdiag<<<1, 256, 0, st>>>(gs, k, k, pivot_tol, w.dscr + 4);
+    count_launch(ctx);
+    for (int kb = 0; kb < k; kb += NBK) {
+        const int nb = std::min(NBK, k - kb);
+        k_chol_panel<<<1, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4, w.drop);
+        count_launch(ctx);
+        const int rest = k - kb - nb;
+        if (rest > 0) {
+            dim3 g(cdiv(rest, 32), cdiv(rest, 32));
+            k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb);
+            count_launch(ctx);
+        }
+    }
+    k_keep_scan<<<1, 1, 0, st>>>(w.drop, k, w.keep);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "cholesky");
+    int kc = 0;
+    double *slot = w.hbuf + w.hbuf_elems - 8;   // the front of hbuf holds LOBPCG residuals
+    RS_CUDA(ctx, cudaMemcpyAsync(slot, w.keep + k, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(ctx, cudaStreamSynchronize(st));
+    memcpy(&kc, slot, sizeof(int));
+    if (ndropped) *ndropped = k - kc;
+    if (kc < nkeep)
+        return fail(ctx, RSDFT_E_NOT_SPD, "overlap has %d independent columns, %d wanted", kc, nkeep);
+    const int T = 256;
+    const long long kc2 = (long long)kc * kc;
+    // compact L -> Km, G_H -> Ym
+    k_gather_sq<<<cdiv(kc2, T), T, 0, st>>>(w.Lm, k, w.keep, kc, w.Km, kc);
+    count_launch(ctx);
+    k_gather_sq<<<cdiv(kc2, T), T, 0, st>>>(gh, k, w.keep, kc, w.Ym, kc);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "compaction");
+    // first TRSM: Y = L^-1 G_H
+    RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Ym, kc, kc, st));
+    // second TRSM: K = L^-1 Y^H
+    k_conj_transpose<<<cdiv(kc2, T), T, 0, st>>>(w.Ym, kc, kc, w.Vh, kc);
+    count_launch(ctx);
+    RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Vh, kc, kc, st));
+    k_hermitise<<<cdiv(kc2, T), T, 0, st>>>(w.Vh, kc, kc, w.Ym, kc);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "reduction");
+    // eigenpairs of K (destroys Ym; the reflectors overwrite Vh)
+    RS_TRY(eigh_lowest(ctx, w.Ym, kc, nkeep, lam_dev, w.Zc, nkeep, st));
+    // C = L^-H Z
+    RS_TRY(trsm_upperH(ctx, w.Km, kc, kc, w.Zc, nkeep, nkeep, st));
+    RS_CUDA(ctx, cudaMemsetAsync(c_out, 0, (size_t)k * nkeep * sizeof(double2), st));
+    k_place_rows<<<cdiv((long long)kc * nkeep, T), T, 0, st>>>(w.Zc, kc, nkeep, w.keep, c_out);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "back-substitution");
+    return RSDFT_OK;
+}
+
+}  // namespace rsdft
+
+using namespace rsdft;
+
+extern "C" {
+
+rsdft_status rsdft_rayleigh_ritz(rsdft_ctx *ctx, const void *gh_dev, const void *gs_dev, int k,
+                                 int nkeep, double pivot_tol, double *lam_host, void *c_dev,
+                                 int *ndropped_host, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (k <= 0 || nkeep <= 0 || nkeep > k || !gh_dev || !gs_dev || !lam_host || !c_dev)
+        return fail(ctx, RSDFT_E_INVALID, "bad rayleigh_ritz arguments");
+    RS_TRY(ensure_workspace(ctx, cdiv(k, 3)));
+    cudaStream_t st = as_stream(stream);
+    int nd = 0;
+    RS_TRY(rayleigh_ritz(ctx, (const double2 *)gh_dev, (const double2 *)gs_dev, k, nkeep, pivot_tol,
+                         ctx->ws.lam, (double2 *)c_dev, &nd, st));
+    RS_CUDA(ctx, cudaMemcpyAsync(lam_host, ctx->ws.lam, nkeep * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ndropped_host) *ndropped_host = nd;
+    return RSDFT_OK;
+}
+
+rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, double *lam_host,
+                        void *z_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (k <= 0 || nkeep <= 0 || nkeep > k || !a_dev || !lam_host || !z_dev)
+        return fail(ctx, RSDFT_E_INVALID, "bad eigh arguments");
+    RS_TRY(ensure_workspace(ctx, cdiv(k, 3)));
+    cudaStream_t st = as_stream(stream);
+    RS_CUDA(ctx, cudaMemcpyAsync(ctx->ws.Ym, a_dev, (size_t)k * k * sizeof(double2),
+                                 cudaMemcpyDeviceToDevice, st));
+    RS_TRY(eigh_lowest(ctx, ctx->ws.Ym, k, nkeep, ctx->ws.lam, (double2 *)z_dev, nkeep, st));
+    RS_CUDA(ctx, cudaMemcpyAsync(lam_host, ctx->ws.lam, nkeep * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(ctx, cudaStreamSynchronize(st));
+    return RSDFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,310 @@
+// GEMM-shaped kernels of the LOBPCG iteration (SCF task (2)), FP64 complex:
+//   gram   : G[i][j] = scale * sum_r conj(A_i(r)) B_j(r)  (reduction length n,
+//            split-K over CTAs, partial tiles reduced in a fixed order)
+//   rotate : out[b][r] = base[b][r] + sign * sum_i c[i][b] Y_i(r)
+// Both read the orbital blocks in their native band-major layout.
+#include <algorithm>
+
+#include "rsdft_internal.h"
+
+namespace rsdft {
+
+constexpr int GT = 64;      // output tile edge
+constexpr int GKC = 16;     // reduction chunk per shared-memory stage
+constexpr int GTHREADS = 256;
+
+__device__ __forceinline__ const double2 *row_of(const RowBlocks &rb, int i, long long n) {
+    if (i < rb.cnt[0]) return rb.ptr[0] + (size_t)i * n;
+    i -= rb.cnt[0];
+    if (i < rb.cnt[1]) return rb.ptr[1] + (size_t)i * n;
+    i -= rb.cnt[1];
+    return rb.ptr[2] + (size_t)i * n;
+}
+
+// Upper-triangular tile enumeration: t -> (ti, tj), ti <= tj, row by row.
+__device__ __forceinline__ void upper_tile(int t, int T, int &ti, int &tj) {
+    int i = 0;
+    while (t >= T - i) { t -= T - i; ++i; }
+    ti = i;
+    tj = i + t;
+}
+
+__global__ void __launch_bounds__(GTHREADS)
+k_gram_partial(RowBlocks A, RowBlocks B, int na, int nb, long long n, int hermitian, int Ti,
+               int Tj, long long kchunk, double2 *__restrict__ part) {
+    __shared__ double2 As[GKC][GT + 1];
+    __shared__ double2 Bs[GKC][GT + 1];
+    int ti, tj;
+    if (hermitian) upper_tile(blockIdx.x, Ti, ti, tj);
+    else { ti = blockIdx.x / Tj; tj = blockIdx.x % Tj; }
+    const int split = blockIdx.y;
+    const long long k0 = (long long)split * kchunk;
+    const long long k1 = min(n, k0 + kchunk);
+    const int i0 = ti * GT, j0 = tj * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double ar[4][4], ai[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.0;
+    // loader mapping: 64 rows x 16 k per stage, 4 elements per thread
+    const int lrow = threadIdx.x >> 2, lk = (threadIdx.x & 3) * 4;
+    const double2 *arow = (i0 + lrow < na) ? row_of(A, i0 + lrow, n) : nullptr;
+    const double2 *brow = (j0 + lrow < nb) ? row_of(B, j0 + lrow, n) : nullptr;
+    for (long long kb = k0; kb < k1; kb += GKC) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long kk = kb + lk + q;
+            double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+            if (kk < k1) {
+                if (arow) va = arow[kk];
+                if (brow) vb = brow[kk];
+            }
+            As[lk + q][lrow] = va;
+            Bs[lk + q][lrow] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GKC; ++k) {
+            double2 a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[k][ty + 16 * q];
+                b[q] = Bs[k][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    // conj(a) * b
+                    ar[p][q] = fma(a[p].x, b[q].x, fma(a[p].y, b[q].y, ar[p][q]));
+                    ai[p][q] = fma(a[p].x, b[q].y, fma(-a[p].y, b[q].x, ai[p][q]));
+                }
+        }
+        __syncthreads();
+    }
+    double2 *pp = part + (size_t)split * na * nb;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = i0 + ty + 16 * p;
+        if (i >= na) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx + 16 * q;
+            if (j < nb) pp[(size_t)i * nb + j] = make_double2(ar[p][q], ai[p][q]);
+        }
+    }
+}
+
+__global__ void k_gram_reduce(const double2 *__restrict__ part, int nsplit, int na, int nb,
+                              int hermitian, double scale, double2 *__restrict__ g, int ldg) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)na * nb) return;
+    const int i = (int)(idx / nb), j = (int)(idx % nb);
+    const size_t stride = (size_t)na * nb;
+    auto sum_at = [&](int r, int c) {
+        double sx = 0.0, sy = 0.0;
+        for (int s = 0; s < nsplit; ++s) {
+            double2 v = part[s * stride + (size_t)r * nb + c];
+            sx += v.x;
+            sy += v.y;
+        }
+        return make_double2(sx, sy);
+    };
+    double2 val;
+    if (!hermitian) {
+        val = sum_at(i, j);
+    } else {
+        const int ti = i / GT, tj = j / GT;
+        if (ti < tj) val = sum_at(i, j);
+        else if (ti > tj) { double2 t = sum_at(j, i); val = make_double2(t.x, -t.y); }
+        else {
+            double2 a = sum_at(i, j), b = sum_at(j, i);
+            val = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        }
+    }
+    g[(size_t)i * ldg + j] = make_double2(val.x * scale, val.y * scale);
+}
+
+static rsdft_status ensure_gram_part(rsdft_ctx *ctx, size_t elems) {
+    Workspace &w = ctx->ws;
+    if (elems <= w.gram_part_elems) return RSDFT_OK;
+    if (w.gram_part) {
+        cudaFree(w.gram_part);
+        for (auto &p : ctx->owned)
+            if (p == w.gram_part) p = nullptr;
+    }
+    w.gram_part = nullptr;
+    w.gram_part_elems = 0;
+    RS_TRY(dev_alloc(ctx, (void **)&w.gram_part, elems * sizeof(double2)));
+    w.gram_part_elems = elems;
+    return RSDFT_OK;
+}
+
+rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
+                  bool hermitian, double scale, cudaStream_t st) {
+    const int na = A.cnt[0] + A.cnt[1] + A.cnt[2];
+    const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
+    if (na <= 0 || nb <= 0) return RSDFT_OK;
+    if (hermitian && na != nb) return fail(ctx, RSDFT_E_INVALID, "hermitian gram needs na == nb");
+    const int Ti = cdiv(na, GT), Tj = cdiv(nb, GT);
+    const int tiles = hermitian ? Ti * (Ti + 1) / 2 : Ti * Tj;
+    const long long n = ctx->n;
+    // split the reduction so that the grid fills the GPU a few times over
+    int nsplit = cdiv(1216, tiles);
+    nsplit = std::max(1, std::min(nsplit, 16));
+    while (nsplit > 1 && n / nsplit < 2048) --nsplit;
+    long long kchunk = (n + nsplit - 1) / nsplit;
+    kchunk = (kchunk + GKC - 1) / GKC * GKC;
+    nsplit = (int)((n + kchunk - 1) / kchunk);
+    RS_TRY(ensure_gram_part(ctx, (size_t)nsplit * na * nb));
+    dim3 grid(tiles, nsplit);
+    {
+        const bool same = A.ptr[0] == B.ptr[0] && A.ptr[1] == B.ptr[1] && A.ptr[2] == B.ptr[2];
+        const double entries = hermitian ? 0.5 * na * (na + 1.0) : (double)na * nb;
+        ProfScope ps(ctx, RSDFT_K_GRAM, 8.0 * (double)n * entries,
+                     16.0 * (double)n * (same ? na : na + nb), st);
+        k_gram_partial<<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj, kchunk,
+                                                  ctx->ws.gram_part);
+    }
+    RS_LAUNCHED(ctx, "k_gram_partial");
+    const long long tot = (long long)na * nb;
+    k_gram_reduce<<<cdiv(tot, 256), 256, 0, st>>>(ctx->ws.gram_part, nsplit, na, nb,
+                                                   hermitian ? 1 : 0, scale, g, ldg);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_gram_reduce");
+    return RSDFT_OK;
+}
+
+// ---- rotation ----------------------------------------------------------------------
+// Tile: 64 bands x 64 points.  Rows of Y are consumed block 1, block 2, then
+// block 0, so that out1 (the W/P part alone) is available before the X part is
+// added.
+__global__ void __launch_bounds__(GTHREADS)
+k_rotate(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long long n,
+         const double2 *base, int sign, double2 *out0, double2 *out1) {
+    __shared__ double2 Cs[GKC][GT + 1];
+    __shared__ double2 Ys[GKC][GT + 1];
+    const int b0 = blockIdx.x * GT;
+    const long long r0 = (long long)blockIdx.y * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double accx[4][4], accy[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) accx[p][q] = accy[p][q] = 0.0;
+    const int order[3] = {1, 2, 0};
+    int rowstart[3];
+    rowstart[0] = 0;
+    rowstart[1] = Y.cnt[0];
+    rowstart[2] = Y.cnt[0] + Y.cnt[1];
+    for (int oi = 0; oi < 3; ++oi) {
+        const int blk = order[oi];
+        const int cnt = Y.cnt[blk];
+        const double2 *yb = Y.ptr[blk];
+        const int crow0 = rowstart[blk];
+        for (int kb = 0; kb < cnt; kb += GKC) {
+            for (int idx = threadIdx.x; idx < GKC * GT; idx += GTHREADS) {
+                const int kk = idx / GT, cc = idx % GT;
+                const int i = kb + kk;
+                double2 cv = make_double2(0.0, 0.0), yv = make_double2(0.0, 0.0);
+                if (i < cnt) {
+                    if (b0 + cc < m) cv = c[(size_t)(crow0 + i) * ldc + b0 + cc];
+                    if (r0 + cc < n) yv = yb[(size_t)i * n + r0 + cc];
+                }
+                Cs[kk][cc] = cv;
+                Ys[kk][cc] = yv;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < GKC; ++k) {
+                double2 cv[4], yv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    cv[q] = Cs[k][ty + 16 * q];
+                    yv[q] = Ys[k][tx + 16 * q];
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        accx[p][q] = fma(cv[p].x, yv[q].x, fma(-cv[p].y, yv[q].y, accx[p][q]));
+                        accy[p][q] = fma(cv[p].x, yv[q].y, fma(cv[p].y, yv[q].x, accy[p][q]));
+                    }
+            }
+            __syncthreads();
+        }
+        if (oi == 1 && out1) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int b = b0 + ty + 16 * p;
+                if (b >= m) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const long long r = r0 + tx + 16 * q;
+                    if (r < n) out1[(size_t)b * n + r] = make_double2(accx[p][q], accy[p][q]);
+                }
+            }
+        }
+    }
+    const double sg = (double)sign;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int b = b0 + ty + 16 * p;
+        if (b >= m) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long r = r0 + tx + 16 * q;
+            if (r >= n) continue;
+            double ox = sg * accx[p][q], oy = sg * accy[p][q];
+            if (base) {
+                const double2 bv = base[(size_t)b * n + r];
+                ox += bv.x;
+                oy += bv.y;
+            }
+            out0[(size_t)b * n + r] = make_double2(ox, oy);
+        }
+    }
+}
+
+rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ldc, int m,
+                    const double2 *base, int sign, double2 *out0, double2 *out1,
+                    cudaStream_t st) {
+    if (m <= 0) return RSDFT_OK;
+    dim3 grid(cdiv(m, GT), cdiv(ctx->n, GT));
+    const int k = Y.cnt[0] + Y.cnt[1] + Y.cnt[2];
+    ProfScope ps(ctx, RSDFT_K_ROTATE, 8.0 * (double)ctx->n * k * m,
+                 16.0 * (double)ctx->n * (k + m + (out1 ? m : 0) + (base ? m : 0)), st);
+    k_rotate<<<grid, GTHREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base, sign, out0, out1);
+    RS_LAUNCHED(ctx, "k_rotate");
+    return RSDFT_OK;
+}
+
+}  // namespace rsdft
+
+using namespace rsdft;
+
+extern "C" {
+
+rsdft_status rsdft_gram(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
+                        void *g_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (na < 0 || nb < 0 || ((na > 0 && nb > 0) && (!a_dev || !b_dev || !g_dev)))
+        return fail(ctx, RSDFT_E_INVALID, "bad gram arguments");
+    RowBlocks A{{(const double2 *)a_dev, nullptr, nullptr}, {na, 0, 0}};
+    RowBlocks B{{(const double2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
+    return gram(ctx, A, B, (double2 *)g_dev, nb, false, ctx->dV, as_stream(stream));
+}
+
+rsdft_status rsdft_rotate(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
+                          const void *base_dev, int sign, void *out_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (k < 0 || m < 0 || (m > 0 && (!out_dev || (k > 0 && (!y_dev || !c_dev)))) ||
+        (sign != 1 && sign != -1))
+        return fail(ctx, RSDFT_E_INVALID, "bad rotate arguments");
+    RowBlocks Y{{(const double2 *)y_dev, nullptr, nullptr}, {k, 0, 0}};
+    return rotate(ctx, Y, (const double2 *)c_dev, m, m, (const double2 *)base_dev, sign,
+                  (double2 *)out_dev, nullptr, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal declarations of the rsdft CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rsdft.h"
+
+namespace rsdft {
+
+constexpr int MAX_N = 128;          // largest grid dimension
+constexpr int MAX_STAGES = 8;       // FFT stages per axis
+
+// One axis of the 3D FFT: N = prod radix[s]; stage s works on blocks of
+// length len[s] with sub-stride sub[s] = len[s] / radix[s].  Forward stages run
+// in order (decimation in frequency, natural order in, digit-reversed out),
+// inverse stages in reverse order (decimation in time, digit-reversed in,
+// natural out), so a forward-scale-inverse round trip needs no reordering.
+struct AxisPlan {
+    int N;
+    int nstage;
+    int radix[MAX_STAGES];
+    int len[MAX_STAGES];
+    int sub[MAX_STAGES];
+};
+
+struct Fft3Plan {
+    AxisPlan ax[3];          // x, y, z
+    const double2 *tw64[3];  // [N] exp(-2 pi i k / N), device
+    const float2 *tw32[3];
+    const double *g2pos[3];  // G_a^2 at each digit-reversed position, device
+};
+
+// Device views handed to kernels.
+struct ProjTables {
+    int natom, nproj;
+    const int *a_start;      // [natom+1] atom-major entry ranges
+    const int *a_idx;        // [nent] grid index
+    const double *a_beta;    // [nent][4] beta values (unused slots 0)
+    const int *c_rowptr;     // [n+1] point-major CSR
+    const int *c_atom;       // [nent]
+    const double *c_beta;    // [nent][4]
+    const double *e_kb;      // [natom*nproj]
+};
+
+struct Workspace {
+    int cap_band = 0;        // bands the buffers are sized for
+    // orbital-sized buffers, each cap_band * n complex128
+    double2 *X = nullptr, *HX = nullptr, *W = nullptr, *HW = nullptr, *P = nullptr,
+            *HP = nullptr, *T1 = nullptr, *Xn = nullptr, *HXn = nullptr, *Pn = nullptr,
+            *HPn = nullptr;
+    // projector coefficients [cap_band][natom*nproj]
+    double2 *proj = nullptr;
+    // subspace: k = 3 * cap_band
+    int cap_k = 0;
+    double2 *GS = nullptr, *GH = nullptr, *C = nullptr, *Cfull = nullptr;
+    double2 *gram_part = nullptr;  size_t gram_part_elems = 0;
+    // dense core scratch
+    double2 *Lm = nullptr, *Km = nullptr, *Ym = nullptr, *Vh = nullptr, *Zc = nullptr;
+    double2 *tau = nullptr, *wv = nullptr;
+    double *d = nullptr, *e = nullptr, *lam = nullptr, *zt = nullptr, *dscr = nullptr;
+    double *fac = nullptr;   // inverse-iteration factors [k][5][k]
+    int *drop = nullptr, *keep = nullptr, *ikeep = nullptr;
+    // per-band vectors [cap_band]
+    double *theta = nullptr, *res = nullptr, *vexp = nullptr, *tkin = nullptr, *nrm = nullptr;
+    int *act = nullptr;
+    double *hbuf = nullptr;  // pinned host scratch
+    size_t hbuf_elems = 0;
+};
+
+struct ScfWork {
+    int ready = 0;
+    int nband = 0;
+    int step = 0;
+    double *rho_in = nullptr, *rho_out = nullptr, *vh = nullptr, *eps = nullptr, *vxc = nullptr;
+    double *veff = nullptr;
+    double *hist_rho = nullptr, *hist_f = nullptr;   // [depth+1][n]
+    int hist_count = 0, hist_cap = 0;
+    double *f = nullptr, *eig = nullptr;             // [nband]
+    double *red = nullptr;                           // reduction scratch
+    double2 *cbuf = nullptr;                         // [n] complex scratch (FFT)
+};
+
+struct Profiler {
+    bool on = false;
+    struct Rec { cudaEvent_t a, b; int id; double flops, bytes; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[RSDFT_K_COUNT] = {}, flops[RSDFT_K_COUNT] = {}, bytes[RSDFT_K_COUNT] = {};
+    long long count[RSDFT_K_COUNT] = {};
+};
+
+}  // namespace rsdft
+
+struct rsdft_ctx {
+    int N[3];
+    double L[3];
+    long long n;
+    double dV;
+    rsdft::Fft3Plan fft;
+    std::vector<void *> owned;       // device allocations freed at destroy
+    double *vloc = nullptr;          // [n] the V_loc given at create
+    double *v = nullptr;             // [n] potential used by H
+    rsdft::ProjTables pt{};
+    long long nent = 0;
+    rsdft::Workspace ws;
+    rsdft::ScfWork scf;
+    rsdft::Profiler prof;
+    long long launches = 0;          // every kernel launched on this context
+    std::string err;
+};
+
+namespace rsdft {
+
+// ---- error helpers --------------------------------------------------------
+rsdft_status fail(rsdft_ctx *ctx, rsdft_status st, const char *fmt, ...);
+rsdft_status cuda_check(rsdft_ctx *ctx, cudaError_t e, const char *what);
+#define RS_CUDA(ctx, call)                                                     \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::rsdft::cuda_check((ctx), e_, #call);   \
+    } while (0)
+#define RS_LAUNCHED(ctx, what)                                                 \
+    do {                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess) return ::rsdft::cuda_check((ctx), e_, what);    \
+    } while (0)
+#define RS_TRY(expr)                                                           \
+    do {                                                                       \
+        rsdft_status s_ = (expr);                                              \
+        if (s_ != RSDFT_OK) return s_;                                         \
+    } while (0)
+
+rsdft_status dev_alloc(rsdft_ctx *ctx, void **p, size_t bytes);
+
+// Brackets the launches of one hot kernel with CUDA events when profiling is
+// on; always counts the launches.
+struct ProfScope {
+    rsdft_ctx *ctx;
+    cudaStream_t st;
+    int id;
+    double flops, bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(rsdft_ctx *c, int kid, double fl, double by, cudaStream_t s, int nlaunch = 1);
+    ~ProfScope();
+};
+inline void count_launch(rsdft_ctx *ctx, int n = 1) { ctx->launches += n; }
+rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband);
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---- FFT / H psi (fft.cu) ---------------------------------------------------
+enum class Mid { Kinetic, Tpa, Hartree, Scale };
+enum class Src { Plain, Residual, RealField };
+// Forward xy-plane pass: src -> dst ([nb][n] complex).  Src::Residual reads
+// hx[act[b]] - theta[act[b]] x[act[b]]; Src::RealField reads a real [n] field
+// (nb must be 1).
+rsdft_status fft_xy_forward(rsdft_ctx *ctx, Src kind, const double2 *src, const double2 *src2,
+                            const double *theta, const int *act, const double *rsrc,
+                            double2 *dst, int nb, cudaStream_t st);
+// z pass: forward z FFT, multiply by the Mid factor, inverse z FFT (in place).
+rsdft_status fft_z_mid(rsdft_ctx *ctx, Mid mid, double2 *buf, const double *tkin, int nb,
+                       cudaStream_t st);
+// Inverse xy pass.  When psi != nullptr: out = T psi + V psi + NL(p) (H psi);
+// else out = buf transformed (plain).  When rout != nullptr (nb == 1) the real
+// part is written to rout instead.
+rsdft_status fft_xy_inverse(rsdft_ctx *ctx, const double2 *buf, const double2 *psi,
+                            const double2 *p, double2 *out, double *rout, int nb,
+                            cudaStream_t st);
+rsdft_status project(rsdft_ctx *ctx, const double2 *psi, double2 *p, int nb, cudaStream_t st);
+rsdft_status apply_h64(rsdft_ctx *ctx, const double2 *psi, double2 *hpsi, int nb,
+                       cudaStream_t st);
+
+// ---- GEMM-shaped kernels (gemm.cu) -------------------------------------------
+struct RowBlocks {
+    const double2 *ptr[3];
+    int cnt[3];
+};
+// g[i][j] = scale * sum_r conj(A_i) B_j over rows of A (na) and B (nb).
+// hermitian: A and B index the same basis; only tiles with ti <= tj are formed
+// and g is completed as a Hermitian matrix.  ldg = leading dimension of g.
+rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
+                  bool hermitian, double scale, cudaStream_t st);
+// out1 (optional) = sum over blocks 1..2 of c rows; out0 = out1 + block-0 part
+// (+ sign * ... and base handling as in rsdft_rotate).  c is [k][ldc].
+rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ldc, int m,
+                    const double2 *base, int sign, double2 *out0, double2 *out1,
+                    cudaStream_t st);
+
+// ---- dense core (dense.cu) ----------------------------------------------------
+rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,
+                           int nkeep, double pivot_tol, double *lam_dev, double2 *c_out,
+                           int *ndropped, cudaStream_t st);
+rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
+                         double2 *z, int ldz, cudaStream_t st);
+
+// ---- small vector kernels (lobpcg.cu / scf.cu) ----------------------------------
+rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st);
+
+}  // namespace rsdft

@@ -1,0 +1,46 @@
+"""Shared helpers of the GPU parity tests: build the CUDA context and the
+oracle Hamiltonian for the same workload, move arrays between host and device."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.grid import Grid, kb_projectors, local_potential  # noqa: E402
+from oracle.hamiltonian import Hamiltonian  # noqa: E402
+
+from paper_2512_04447_gb300 import rsdft as R  # noqa: E402
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t) -> np.ndarray:
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def pair(wl):
+    """(CUDA context, oracle Hamiltonian, oracle V_loc) for a workload; each
+    side builds V_loc and the projectors with its own code."""
+    g = Grid(L=wl.L, N=wl.N)
+    v = local_potential(g, wl.positions, wl.Z, wl.sigma)
+    P = kb_projectors(g, wl.positions, wl.rc, wl.rcut, wl.e_kb(), wl.nproj)
+    ham = Hamiltonian(g, v, P)
+    ctx = R.context_for(wl)
+    return ctx, ham, v
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def subspace_distance(Xa, Xb, dV):
+    """sin of the largest principal angle between span(Xa) and span(Xb)."""
+    s = np.linalg.svd((Xa.conj() @ Xb.T) * dV, compute_uv=False)
+    return float(np.sqrt(max(0.0, 1.0 - np.min(s) ** 2)))
