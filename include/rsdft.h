@@ -88,8 +88,9 @@ rsdft_status rsdft_create(const rsdft_cell *cell, const rsdft_grid *grid,
                           rsdft_ctx **out);
 void rsdft_destroy(rsdft_ctx *ctx);
 
-/* Text of the last error on ctx (or of the last failed rsdft_create on this
- * thread when ctx is NULL).  Valid until the next call on the same ctx. */
+/* Text of the last error on ctx (or, when ctx is NULL, of the last failed
+ * rsdft_create or context-free call on this thread).  Valid until the next
+ * call on the same ctx. */
 const char *rsdft_last_error(const rsdft_ctx *ctx);
 
 /* Input builder for the synthetic workloads: V(r) = sum_a -Z exp(-|d_a|^2 /
@@ -135,6 +136,27 @@ rsdft_status rsdft_precondition_tpa(rsdft_ctx *ctx, const void *r_dev, void *w_d
  */
 rsdft_status rsdft_gram(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
                         void *g_dev, void *stream);
+
+/* Gram matrix without any device allocation, for callers that cannot call
+ * cudaMalloc: for example a time-stepping driver (RS-TDDFT, Ehrenfest MD)
+ * that reserves all device memory before its loop and must not allocate or
+ * free inside it, because each allocation synchronises the device and
+ * fragments its fixed pool.  The paper has no counterpart; it is an extra
+ * entry point of this library.  Needs no context.
+ *   g[i][j] = scale * sum_{r<n} conj(a_i(r)) b_j(r); a_dev: [na][n],
+ *   b_dev: [nb][n], g_dev: [na][nb] row-major, complex128, caller-owned
+ *   device memory.
+ * The split-K partial sums go to one fixed device array of 2^21 complex128
+ * entries (32 MiB) inside the library, held by every GPU that loads it until
+ * the process exits; na * nb above 2^21 is rejected with RSDFT_E_INVALID.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other host threads on the same device) race and give wrong results.
+ * No earlier contents are read (every entry used is written first).  Errors:
+ * rsdft_last_error(NULL). */
+rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int nb, long long n,
+                               double scale, void *g_dev, void *stream);
 
 /* Rotation out[b] = sum_i c[i][b] y[i] (+ base[b] when base_dev != NULL;
  * base may alias out).  y_dev: [k][n]; c_dev: [k][m] row-major;

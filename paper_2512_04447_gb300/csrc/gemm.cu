@@ -4,6 +4,7 @@
 //   rotate : out[b][r] = base[b][r] + sign * sum_i c[i][b] Y_i(r)
 // Both read the orbital blocks in their native band-major layout.
 #include <algorithm>
+#include <mutex>
 
 #include "rsdft_internal.h"
 
@@ -280,11 +281,81 @@ rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ld
     return RSDFT_OK;
 }
 
+// ---- Gram without allocation -------------------------------------------------------
+// Split-K partial tiles of rsdft_gram_static live in this fixed array, which
+// every GPU that loads the library holds until the process exits.
+constexpr size_t STATIC_GRAM_ELEMS = (size_t)1 << 21;   // complex128 entries, 32 MiB
+static __device__ __align__(256) double2 g_static_gram_part[STATIC_GRAM_ELEMS];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+static std::mutex g_static_mu;
+static double2 *g_static_addr[STATIC_MAX_DEVICES] = {};
+
+// Device address of g_static_gram_part on the current device, looked up once
+// per device (the host-side name is only a stand-in for it).
+static rsdft_status static_gram_scratch(double2 **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, RSDFT_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES)
+        return fail(nullptr, RSDFT_E_INVALID, "device %d beyond the %d supported", dev, STATIC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_gram_part);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(nullptr, RSDFT_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        }
+        g_static_addr[dev] = static_cast<double2 *>(p);
+    }
+    *out = g_static_addr[dev];
+    return RSDFT_OK;
+}
+
 }  // namespace rsdft
 
 using namespace rsdft;
 
 extern "C" {
+
+rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int nb, long long n,
+                               double scale, void *g_dev, void *stream) {
+    if (na < 0 || nb < 0 || n <= 0)
+        return fail(nullptr, RSDFT_E_INVALID, "need na >= 0, nb >= 0, n > 0");
+    if (na == 0 || nb == 0) return RSDFT_OK;
+    if (!a_dev || !b_dev || !g_dev) return fail(nullptr, RSDFT_E_INVALID, "null pointer argument");
+    if ((size_t)na * (size_t)nb > STATIC_GRAM_ELEMS)
+        return fail(nullptr, RSDFT_E_INVALID,
+                    "na*nb = %lld exceeds the fixed scratch of %zu entries (rsdft_gram_static)",
+                    (long long)na * nb, STATIC_GRAM_ELEMS);
+    double2 *part = nullptr;
+    RS_TRY(static_gram_scratch(&part));
+    cudaStream_t st = as_stream(stream);
+    const int Ti = cdiv(na, GT), Tj = cdiv(nb, GT);
+    const int tiles = Ti * Tj;
+    int nsplit = std::max(1, std::min(cdiv(1216, tiles), 16));
+    while (nsplit > 1 && n / nsplit < 2048) --nsplit;
+    nsplit = std::max(1, std::min<int>(nsplit, (int)(STATIC_GRAM_ELEMS / ((size_t)na * nb))));
+    long long kchunk = (n + nsplit - 1) / nsplit;
+    kchunk = (kchunk + GKC - 1) / GKC * GKC;
+    nsplit = (int)((n + kchunk - 1) / kchunk);
+    RowBlocks A{{(const double2 *)a_dev, nullptr, nullptr}, {na, 0, 0}};
+    RowBlocks B{{(const double2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
+    // every partial entry the reduction reads is written by this launch first,
+    // so nothing left by an earlier call is read
+    k_gram_partial<<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_partial: %s", cudaGetErrorString(e));
+    k_gram_reduce<<<cdiv((long long)na * nb, 256), 256, 0, st>>>(part, nsplit, na, nb, 0, scale,
+                                                                 (double2 *)g_dev, nb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_reduce: %s", cudaGetErrorString(e));
+    return RSDFT_OK;
+}
 
 rsdft_status rsdft_gram(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
                         void *g_dev, void *stream) {

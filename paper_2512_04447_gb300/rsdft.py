@@ -90,6 +90,7 @@ _PROTOS = {
     "rsdft_project": (ip, [vp, vp, vp, ip, vp]),
     "rsdft_precondition_tpa": (ip, [vp, vp, vp, vp, ip, vp]),
     "rsdft_gram": (ip, [vp, vp, ip, vp, ip, vp, vp]),
+    "rsdft_gram_static": (ip, [vp, ip, vp, ip, C.c_longlong, dp, vp, vp]),
     "rsdft_rotate": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_rayleigh_ritz": (ip, [vp, vp, vp, ip, ip, dp, vp, vp, vp, vp]),
     "rsdft_eigh": (ip, [vp, vp, ip, ip, vp, vp, vp]),
@@ -170,6 +171,15 @@ def gaussian_vloc(L, N, positions, Z: float, sigma: float) -> np.ndarray:
     if st != OK:
         raise RsdftError(st, lib().rsdft_last_error(None).decode())
     return out
+
+
+def gram_static(a, b, g, scale: float) -> None:
+    """rsdft_gram_static: g = scale * conj(a) @ b.T with no device allocation
+    (the library's fixed scratch array holds the partial sums)."""
+    st = lib().rsdft_gram_static(_ptr(a), a.shape[0], _ptr(b), b.shape[0], a.shape[1], float(scale),
+                                 _ptr(g), _stream())
+    if st != OK:
+        raise RsdftError(st, lib().rsdft_last_error(None).decode())
 
 
 class Context:
