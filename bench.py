@@ -158,8 +158,86 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# FP32 CUDA-core peak: 128 FP32 lanes per SM, one FMA (2 flop) each per clock.
+FP32_FLOP_PER_CLK_PER_SM = 256.0
+
+
+def reduce_max(values, dist=None, device="cpu"):
+    """Element-wise max of a list of floats over all ranks (identity on one)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_value(total_ms_max, steps, world):
+    """Whole-job seconds per SCF step: world * steps steps done in total_ms_max."""
+    return total_ms_max / 1e3 / (steps * world)
+
+
+def kernel_roofline(name, d, precision, sm_mhz, hbm_gbs):
+    """Bound, achieved and peak of one profiled kernel id.  GEMM-shaped kernels
+    and the FP64 FFT passes are ALU-bound (FP64 or FP32 CUDA cores); the FP32
+    FFT passes and the projector gather are HBM-bound."""
+    s = d["ms"] / 1e3
+    if s <= 0 or d["launches"] == 0:
+        return None
+    fp32 = precision == "mixed"
+    alu = name in ("gram", "rotate") or (name.startswith("fft") and not fp32)
+    per_launch_s = s / d["launches"]
+    if alu:
+        per = FP32_FLOP_PER_CLK_PER_SM if fp32 else FP64_FLOP_PER_CLK_PER_SM
+        peak = NUM_SM * per * sm_mhz * 1e6 / 1e12
+        ach = d["flops"] / s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "avg_launch_ms": per_launch_s * 1e3,
+                "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+                "peak_source": f"{'FP32' if fp32 else 'FP64'} ALU: {NUM_SM} SMs x {per:g} flop/clk "
+                               f"x {sm_mhz:g} MHz (unit counts and max clock)"}
+    ach = d["bytes"] / s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": ach / hbm_gbs, "avg_launch_ms": per_launch_s * 1e3,
+            "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, measured)"}
+
+
+def time_form(ctx, R, torch, x0, wl, precision, args, barrier, stream):
+    """First (converged) SCF step, warm-up, then the timed steps of one form."""
+    prec = R.MIXED if precision == "mixed" else R.FP64
+    opts = ctx.scf_opts(n_electrons=wl.n_electrons, kT=wl.kT, beta=0.3, depth=4, k_lobpcg=3,
+                        first_maxit=200, tol=1e-6, precision=prec)
+    x = torch.from_numpy(x0).cuda()
+    ctx.scf_init(wl.nband, opts)
+    barrier()
+    t0 = time.perf_counter()
+    out0, eig0, _ = ctx.scf_step(x, opts)
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        ctx.scf_step(x, opts)
+    ctx.profile_enable(True)
+    launches0 = ctx.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.nvtx.range_push(f"timed_{precision}")
+    ev[0].record(stream)
+    outs = []
+    for k in range(args.steps):
+        o, eig, occ = ctx.scf_step(x, opts)
+        ev[k + 1].record(stream)
+        outs.append(o.as_dict())
+    barrier()
+    torch.cuda.nvtx.range_pop()
+    launches = ctx.launch_count() - launches0
+    total_ms = ev[0].elapsed_time(ev[-1])
+    kern = {name: ctx.profile_read(kid) for kid, name in enumerate(R.KERNEL_NAMES)}
+    ctx.profile_enable(False)
+    return {"x": x, "opts": opts, "t_first": t_first, "first_iters": out0.lobpcg_iterations,
+            "eig0": eig0, "total_ms": total_ms, "launches": launches, "kern": kern, "outs": outs}
+
+
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
 
     import workloads
@@ -172,10 +250,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     wl = workloads.REGISTRY[WORKLOAD](seed=rank)
     ctx = R.context_for(wl)
-    opts = ctx.scf_opts(n_electrons=wl.n_electrons, kT=wl.kT, beta=0.3, depth=4, k_lobpcg=3,
-                        first_maxit=200, tol=1e-6)
     x0 = wl.x0()
-    x = torch.from_numpy(x0).cuda()
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -183,38 +258,15 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- first (converged) step: LOBPCG time-to-1e-6 Ha
-    ctx.scf_init(wl.nband, opts)
-    barrier()
-    t0 = time.perf_counter()
-    out0, _, _ = ctx.scf_step(x, opts)
-    torch.cuda.synchronize()
-    t_first = time.perf_counter() - t0
-    for _ in range(max(0, args.warmup - 1)):
-        ctx.scf_step(x, opts)
-    # ---- timed region (inputs resident in HBM; X = 604 MB > 129 MB L2)
+    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    head = forms[-1]            # the form the headline value is quoted on
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    time.sleep(0.5)
-    ctx.profile_enable(True)
-    launches0 = ctx.launch_count()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
-    ev[0].record(stream)
-    outs = []
-    for k in range(args.steps):
-        o, eig, occ = ctx.scf_step(x, opts)
-        ev[k + 1].record(stream)
-        outs.append(o.as_dict())
-    barrier()
-    launches = ctx.launch_count() - launches0
-    total_ms = ev[0].elapsed_time(ev[-1])
-    kern = {}
-    for kid, name in enumerate(R.KERNEL_NAMES):
-        kern[name] = ctx.profile_read(kid)
-    ctx.profile_enable(False)
+    res = {f: time_form(ctx, R, torch, x0, wl, f, args, barrier, stream) for f in forms}
     clocks = sampler.stop()
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (headline form)
+    x = res[head]["x"]
+    opts = res[head]["opts"]
     xh = torch.empty_like(x, device="cpu").pin_memory()
     xh.copy_(x)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -223,66 +275,68 @@ def run_ours(args, rank, world, local_rank):
     e0.record(stream)
     for _ in range(args.steps):
         x.copy_(xh, non_blocking=True)
-        o, eig, occ = ctx.scf_step(x, opts)      # returns energies + eigenvalues on the host
+        ctx.scf_step(x, opts)      # returns energies and eigenvalues on the host
         xh.copy_(x, non_blocking=True)
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
     # ---- max over ranks
-    tt = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(tt[0]), float(tt[1])
+    vals = reduce_max([res[f]["total_ms"] for f in forms] + [e2e_ms], dist, "cuda")
+    for f, v in zip(forms, vals):
+        res[f]["total_ms"] = v
+    e2e_ms = vals[-1]
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    ms_step = total_ms / args.steps
-    value = total_ms / 1e3 / (args.steps * world)
-    e2e_value = e2e_ms / 1e3 / (args.steps * world)
-    # ---- roofline of the dominant kernel
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    kd = kern[dom]
-    per_launch_s = kd["ms"] / 1e3 / max(1, kd["launches"])
-    achieved_tf = kd["flops"] / max(1, kd["launches"]) / per_launch_s / 1e12
-    peak_tf = fp64_peak_tflops(sm_max)
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
-                "peak_source": f"FP64 ALU: {NUM_SM} SMs x {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk "
-                               f"x {sm_max:g} MHz (derived from unit counts and max clock)",
-                "algorithmic_flops_per_launch": kd["flops"] / max(1, kd["launches"]),
-                "avg_launch_ms": per_launch_s * 1e3}
-    kernels = {}
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    for k, d in kern.items():
-        if d["launches"] == 0:
-            continue
-        s = d["ms"] / 1e3
-        kernels[k] = {"ms_total": d["ms"], "launches": d["launches"],
-                      "tflops": d["flops"] / s / 1e12 if s > 0 else None,
-                      "frac_fp64_alu": (d["flops"] / s / 1e12) / peak_tf if s > 0 else None,
-                      "gbs": d["bytes"] / s / 1e9 if s > 0 else None,
-                      "frac_hbm": (d["bytes"] / s / 1e9) / hbm if s > 0 else None}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    hbm = float(peaks.get("hbm_gbs", 6668.2))
+    summary = {}
+    for f in forms:
+        r = res[f]
+        kern = {k: kernel_roofline(k, d, f, sm_max, hbm) for k, d in r["kern"].items()}
+        kern = {k: v for k, v in kern.items() if v is not None}
+        for k, v in kern.items():
+            v["ms_total"] = r["kern"][k]["ms"]
+            v["launches"] = r["kern"][k]["launches"]
+        summary[f] = {"s_per_scf_step": job_value(r["total_ms"], args.steps, world),
+                      "lobpcg_time_to_1e-6_s": r["t_first"],
+                      "first_step_lobpcg_iterations": r["first_iters"],
+                      "gpu_launches": r["launches"], "kernels": kern,
+                      "scf_last": {k: r["outs"][-1][k] for k in ("e_tot", "drho", "step")}}
+    if "fp64" in res and "mixed" in res:
+        import numpy as np
+        summary["mixed"]["first_step_eig_max_abs_diff_vs_fp64"] = float(
+            np.max(np.abs(res["mixed"]["eig0"] - res["fp64"]["eig0"])))
+    # dominant single kernel of the headline form (the dense core is a group of launches)
+    hk = {k: v for k, v in summary[head]["kernels"].items() if k != "dense"}
+    dom = max(hk, key=lambda k: hk[k]["ms_total"])
+    roofline = dict(hk[dom])
+    roofline["traffic"] = None
+    r = res[head]
+    line = {"metric": METRIC, "value": job_value(r["total_ms"], args.steps, world), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: 64 C diamond (2x2x2, a=6.74, L=13.48 bohr), 64^3 "
                                    "grid, 144 bands (128 occupied), Gaussian V_loc Z=4 sigma=0.6, "
                                    "4 KB projectors/atom, LDA + FFT Hartree + Anderson(0.3, depth 4); "
                                    "step = SCF step with 3 LOBPCG iterations",
-                       "precision": "FP64 throughout (mixed form not built)",
+                       "precision": ("mixed: FP32 orbitals for H psi/FFT/Gram/rotation, FP64 norms "
+                                     "and dense core; first solve refined in FP64 to 1e-6 Ha"
+                                     if head == "mixed" else "FP64 throughout"),
+                       "learned_preconditioner": "not built (TPA in both forms)",
                        "l2": "inputs larger than L2 (orbital block 604 MB vs 129 MB L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "lobpcg_time_to_1e-6_s": t_first,
-            "first_step_lobpcg_iterations": out0.lobpcg_iterations,
-            "e2e": {"value": e2e_value, "unit": UNIT,
+            "lobpcg_time_to_1e-6_s": r["t_first"],
+            "first_step_lobpcg_iterations": r["first_iters"],
+            "e2e": {"value": job_value(e2e_ms, args.steps, world), "unit": UNIT,
                     "h2d_bytes_per_step": int(x.numel() * 16),
                     "d2h_bytes_per_step": int(x.numel() * 16 + 2 * wl.nband * 8 + 88)},
-            "gpu_launches": int(launches),
-            "roofline": roofline, "kernels": kernels, "clocks": clocks,
-            "scf_last": {k: outs[-1][k] for k in ("e_tot", "drho", "step")}}
+            "gpu_launches": int(r["launches"]),
+            "roofline": roofline, "forms": summary, "clocks": clocks}
     if world == 1 and not args.no_cpu_baseline:
         dt = oracle_step_seconds(wl)
         line["cpu_baseline"] = {"value": dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -294,6 +348,36 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_profile_case(case):
+    """One small launch of a hot kernel for ncu --set full: a 432-row block on a
+    48^3 grid (764 MB, above the 129 MB L2)."""
+    import numpy as np
+    import torch
+
+    from paper_2512_04447_gb300 import rsdft as R
+    N = (48, 48, 48)
+    ctx = R.Context((10.11,) * 3, N, np.zeros(N[0] * N[1] * N[2]))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    cdt = torch.complex64 if case.endswith("32") else torch.complex128
+    if case.startswith("gram") or case.startswith("rotate"):
+        y = torch.randn(432, ctx.n, dtype=torch.complex128, device="cuda", generator=g)
+        if case.startswith("gram"):
+            gm = torch.empty(432, 432, dtype=torch.complex128, device="cuda")
+            ctx.gram(y, y, gm)
+        else:
+            c = torch.randn(432, 144, dtype=torch.complex128, device="cuda", generator=g)
+            out = torch.empty(144, ctx.n, dtype=torch.complex128, device="cuda")
+            ctx.rotate(y, c, out)
+    elif case.startswith("hpsi"):
+        x = torch.randn(16, ctx.n, dtype=cdt, device="cuda", generator=g)
+        hx = torch.empty_like(x)
+        ctx.apply_h(x, hx, precision=R.MIXED if cdt == torch.complex64 else R.FP64)
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    torch.cuda.synchronize()
+    print(f"profile case {case} done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,7 +385,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--profile-case", default=None,
+                    help="run one small case for ncu (gram, rotate, hpsi, hpsi32) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.warmup < 1:
         ap.error("--warmup must be >= 1 (the first SCF step converges LOBPCG)")
     rank = int(os.environ.get("RANK", 0))

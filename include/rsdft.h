@@ -183,7 +183,11 @@ rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, dou
 
 /* ---------------------------------------------------------------------------
  * LOBPCG for the lowest nband eigenpairs of H (the paper's eigensolver,
- * Knyazev's block method with the Rayleigh-Ritz of Eq. 1).
+ * Knyazev's block method with the Rayleigh-Ritz of Eq. 1).  RSDFT_FP64 keeps
+ * everything in FP64.  RSDFT_MIXED runs H psi, the FFTs, the Gram and rotation
+ * GEMMs on FP32 orbitals (FP32 products, FP64 sums across GEMM blocks) while the
+ * residual norms, Cholesky, triangular solves and eigensolve stay FP64, and
+ * finishes with FP64 iterations to tol.
  * x_dev: in/out [nband][n] complex128 (initial guess in, Ritz vectors out,
  * orthonormal).  eig_host, resnorm_host: [nband].
  */
@@ -192,13 +196,19 @@ typedef struct {
     double tol;            /* stop when max residual over the first nconv <= tol   */
     int nconv;             /* bands checked for tol; <= 0 means nband              */
     int precond;           /* rsdft_precond                                        */
-    int precision;         /* rsdft_precision (RSDFT_FP64 only in this version)    */
+    int precision;         /* rsdft_precision                                      */
     double lock_tol;       /* soft-lock bands with residual <= lock_tol (1e-10)    */
-    double pivot_tol;      /* relative Cholesky pivot floor for G_S (1e-8)         */
+    double pivot_tol;      /* relative Cholesky pivot floor for G_S (1e-8; the FP32
+                              data path of RSDFT_MIXED uses at least 1e-5)        */
+    double switch_tol;     /* RSDFT_MIXED: FP32 data path until the max residual
+                              is <= max(tol, switch_tol) (1e-4) or stagnates (3
+                              iterations gaining < 10%), then FP64 to tol; 0 runs
+                              FP32 iterations to maxit                            */
 } rsdft_lobpcg_opts;
 
 typedef struct {
-    int iterations;        /* full iterations done                                 */
+    int iterations;        /* full iterations done (both phases)                   */
+    int iterations_mixed;  /* of which in the FP32 data path (RSDFT_MIXED)         */
     int converged;         /* 1 if the tolerance test passed                       */
     int dropped;           /* basis columns dropped by the Cholesky, summed        */
     double ms_hpsi, ms_precond, ms_gram, ms_dense, ms_rotate, ms_other;
@@ -227,6 +237,10 @@ typedef struct {
     int first_maxit;       /* iteration cap of the first, converged, solve (200)   */
     double tol;            /* residual tolerance of the first solve (1e-6)         */
     int precond;           /* rsdft_precond                                        */
+    int precision;         /* rsdft_precision of the LOBPCG: RSDFT_MIXED runs the
+                              first solve in the mixed form (FP32 data path to
+                              1e-4, then FP64 to tol) and the later steps' k_lobpcg
+                              iterations on the FP32 data path                    */
 } rsdft_scf_opts;
 
 typedef struct {

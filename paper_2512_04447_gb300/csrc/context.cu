@@ -107,13 +107,16 @@ static rsdft_status build_fft_tables(rsdft_ctx *ctx) {
             double g = gunit * ks;
             g2[pos] = g * g;
         }
-        double2 *d_tw; float2 *d_twf; double *d_g2;
+        std::vector<float> g2f(g2.begin(), g2.end());
+        double2 *d_tw; float2 *d_twf; double *d_g2; float *d_g2f;
         RS_TRY(upload(ctx, &d_tw, tw.data(), N));
         RS_TRY(upload(ctx, &d_twf, twf.data(), N));
         RS_TRY(upload(ctx, &d_g2, g2.data(), N));
+        RS_TRY(upload(ctx, &d_g2f, g2f.data(), N));
         ctx->fft.tw64[a] = d_tw;
         ctx->fft.tw32[a] = d_twf;
         ctx->fft.g2pos[a] = d_g2;
+        ctx->fft.g2pos32[a] = d_g2f;
     }
     return RSDFT_OK;
 }
@@ -201,6 +204,13 @@ static rsdft_status build_projectors(rsdft_ctx *ctx, const rsdft_projectors *pj)
     RS_TRY(upload(ctx, &d_cb, c_beta.data(), c_beta.size()));
     RS_TRY(upload(ctx, &d_e, ekb.data(), ekb.size()));
     ctx->pt = ProjTables{natom, nproj, d_as, d_ai, d_ab, d_rp, d_ca, d_cb, d_e};
+    std::vector<float> abf(a_beta.begin(), a_beta.end()), cbf(c_beta.begin(), c_beta.end()),
+        ekf(ekb.begin(), ekb.end());
+    float *d_abf, *d_cbf, *d_ef;
+    RS_TRY(upload(ctx, &d_abf, abf.data(), abf.size()));
+    RS_TRY(upload(ctx, &d_cbf, cbf.data(), cbf.size()));
+    RS_TRY(upload(ctx, &d_ef, ekf.data(), ekf.size()));
+    ctx->pt32 = ProjT<float>{natom, nproj, d_as, d_ai, d_abf, d_rp, d_ca, d_cbf, d_ef};
     ctx->nent = nent;
     return RSDFT_OK;
 }
@@ -234,7 +244,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
         cudaFree(p);
         ctx->owned.erase(std::remove(ctx->owned.begin(), ctx->owned.end(), p), ctx->owned.end());
     };
-    void *olds[] = {w.X, w.HX, w.W, w.HW, w.P, w.HP, w.T1, w.Xn, w.HXn, w.Pn, w.HPn, w.proj,
+    void *olds[] = {w.X, w.HX, w.W, w.HW, w.P, w.HP, w.T1, w.Xn, w.HXn, w.Pn, w.HPn, w.Xs, w.proj,
                     w.GS, w.GH, w.C, w.Cfull, w.gram_part, w.Lm, w.Km, w.Ym, w.Vh, w.Zc,
                     w.tau, w.wv, w.d, w.e, w.lam, w.zt, w.dscr, w.fac, w.drop, w.keep, w.ikeep,
                     w.theta, w.res, w.vexp, w.tkin, w.nrm, w.act};
@@ -245,6 +255,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     const size_t orb = nb * n * sizeof(double2);
     double2 **orbs[] = {&w.X, &w.HX, &w.W, &w.HW, &w.P, &w.HP, &w.T1, &w.Xn, &w.HXn, &w.Pn, &w.HPn};
     for (double2 **b : orbs) RS_TRY(dev_alloc(ctx, (void **)b, orb));
+    RS_TRY(dev_alloc(ctx, (void **)&w.Xs, nb * n * sizeof(float2)));
     const size_t np = (size_t)std::max(1, ctx->pt.natom * ctx->pt.nproj);
     RS_TRY(dev_alloc(ctx, (void **)&w.proj, nb * np * sizeof(double2)));
     const size_t k = 3 * nb;
@@ -305,6 +316,10 @@ rsdft_status rsdft_create(const rsdft_cell *cell, const rsdft_grid *grid, const 
         return fail(nullptr, RSDFT_E_CUDA, "no CUDA device");
     }
     rsdft_ctx *ctx = new rsdft_ctx();
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->num_sms = 1;
+    }
     for (int a = 0; a < 3; ++a) {
         ctx->N[a] = grid->n[a];
         ctx->L[a] = L[a];
@@ -315,6 +330,7 @@ rsdft_status rsdft_create(const rsdft_cell *cell, const rsdft_grid *grid, const 
     rsdft_status st = build_fft_tables(ctx);
     if (st == RSDFT_OK) st = upload(ctx, &ctx->vloc, v_loc_host, (size_t)ctx->n);
     if (st == RSDFT_OK) st = upload(ctx, &ctx->v, v_loc_host, (size_t)ctx->n);
+    if (st == RSDFT_OK) st = dev_alloc(ctx, (void **)&ctx->v32, (size_t)ctx->n * sizeof(float));
     if (st == RSDFT_OK) {
         rsdft_projectors none{0, nullptr, 1, 1.0, 1.0, nullptr};
         st = build_projectors(ctx, proj ? proj : &none);

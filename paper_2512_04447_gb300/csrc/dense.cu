@@ -444,19 +444,35 @@ __global__ void k_tri_prep(const double *d, const double *e, int k, double *scr)
     scr[3] = DBL_MIN * fmax(1.0, emax2);
 }
 
+// Multisection for the lowest nkeep eigenvalues of T, one warp per eigenvalue
+// j: each round the 32 lanes take Sturm counts at 32 interior points of the
+// bracket [lo, hi] and the bracket shrinks to the sub-interval that holds the
+// j-th eigenvalue (counts are monotone in x, so the lanes with count > j form
+// a suffix).  Stops at a bracket of 4 ulps.
 __global__ void k_bisect(const double *d, int k, int nkeep, const double *scr, double *lam) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nkeep) return;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= nkeep) return;   // whole warps exit together (j is uniform per warp)
     const double *e2 = scr + 8;
     double lo = scr[1], hi = scr[2];
     const double pivmin = scr[3];
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (sturm_count(d, e2, k, mid, pivmin) > j) hi = mid;
-        else lo = mid;
+    for (int round = 0; round < 40; ++round) {
+        if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const int c = sturm_count(d, e2, k, x, pivmin);
+        const unsigned ball = __ballot_sync(0xffffffffu, c > j);
+        const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
+        if (ball == 0u) {
+            lo = __shfl_sync(0xffffffffu, x, 31);
+        } else {
+            const int f = __ffs(ball) - 1;
+            const double xf = __shfl_sync(0xffffffffu, x, f);
+            const double xl = __shfl_sync(0xffffffffu, xprev, f);
+            if (f > 0) lo = xl;
+            hi = xf;
+        }
     }
-    lam[j] = 0.5 * (lo + hi);
+    if (lane == 0) lam[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_uniform(unsigned long long x) {
@@ -632,7 +648,7 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     RS_LAUNCHED(ctx, "householder");
     k_tri_prep<<<1, 1, 0, st>>>(w.d, w.e, k, w.dscr);
     count_launch(ctx);
-    k_bisect<<<cdiv(nkeep, 32), 32, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+    k_bisect<<<cdiv(nkeep, 4), 128, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
     count_launch(ctx);
     k_inverse_iter<<<cdiv(nkeep, 32), 32, 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr, w.fac, w.zt);
     count_launch(ctx);

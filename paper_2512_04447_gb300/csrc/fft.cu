@@ -10,6 +10,7 @@
 // Forward stages leave the spectrum in mixed-radix digit-reversed order and
 // the inverse stages take it back to natural order, so the per-G factor is
 // applied through position-indexed |G|^2 tables and no permutation pass exists.
+#include <algorithm>
 #include <cmath>
 
 #include "rsdft_internal.h"
@@ -171,82 +172,118 @@ __device__ void fft_lines(V *s, const AxisPlan &ax, const V *tw, int nlines, int
 
 constexpr int FFT_THREADS = 512;
 
+// Tables of one precision: twiddles exp(-2 pi i k/N) and G_a^2 at each
+// digit-reversed position.
+template <typename V> struct FftTabs {
+    AxisPlan ax[3];
+    const V *tw[3];
+    const typename Sc<V>::T *g2[3];
+};
+
+static FftTabs<double2> tabs_of(const rsdft_ctx *ctx, double2 *) {
+    FftTabs<double2> t;
+    for (int a = 0; a < 3; ++a) {
+        t.ax[a] = ctx->fft.ax[a];
+        t.tw[a] = ctx->fft.tw64[a];
+        t.g2[a] = ctx->fft.g2pos[a];
+    }
+    return t;
+}
+static FftTabs<float2> tabs_of(const rsdft_ctx *ctx, float2 *) {
+    FftTabs<float2> t;
+    for (int a = 0; a < 3; ++a) {
+        t.ax[a] = ctx->fft.ax[a];
+        t.tw[a] = ctx->fft.tw32[a];
+        t.g2[a] = ctx->fft.g2pos32[a];
+    }
+    return t;
+}
+static const ProjT<double> &proj_of(const rsdft_ctx *ctx, double2 *) { return ctx->pt; }
+static const ProjT<float> &proj_of(const rsdft_ctx *ctx, float2 *) { return ctx->pt32; }
+static const double *v_of(const rsdft_ctx *ctx, double2 *) { return ctx->v; }
+static const float *v_of(const rsdft_ctx *ctx, float2 *) { return ctx->v32; }
+
 // ---- xy forward pass ------------------------------------------------------------
-template <Src SRC>
+template <typename V, Src SRC>
 __global__ void __launch_bounds__(FFT_THREADS)
-k_xy_forward(Fft3Plan plan, const double2 *__restrict__ src, const double2 *__restrict__ src2,
+k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src2,
              const double *__restrict__ theta, const int *__restrict__ act,
-             const double *__restrict__ rsrc, double2 *__restrict__ dst) {
-    extern __shared__ double2 s_plane[];
-    const int Nx = plan.ax[0].N, Ny = plan.ax[1].N, Nz = plan.ax[2].N;
+             const double *__restrict__ rsrc, V *__restrict__ dst) {
+    using T = typename Sc<V>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *s_plane = reinterpret_cast<V *>(smem_raw);
+    const int Nx = tb.ax[0].N, Ny = tb.ax[1].N, Nz = tb.ax[2].N;
     const int z = blockIdx.x, band = blockIdx.y;
     const size_t n = (size_t)Nx * Ny * Nz;
     const size_t plane = (size_t)Nx * Ny;
     const size_t off = (size_t)z * plane;
     if (SRC == Src::Plain) {
-        const double2 *in = src + band * n + off;
+        const V *in = src + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = in[i];
     } else if (SRC == Src::Residual) {
         const int b = act[band];
-        const double th = theta[b];
-        const double2 *hx = src + b * n + off;
-        const double2 *x = src2 + b * n + off;
+        const T th = (T)theta[b];
+        const V *hx = src + b * n + off;
+        const V *x = src2 + b * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
-            double2 h = hx[i], v = x[i];
-            s_plane[i] = make_double2(h.x - th * v.x, h.y - th * v.y);
+            V h = hx[i], v = x[i];
+            s_plane[i] = mk<V>(h.x - th * v.x, h.y - th * v.y);
         }
     } else {
         const double *in = rsrc + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = make_double2(in[i], 0.0);
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = mk<V>((T)in[i], (T)0);
     }
     __syncthreads();
-    fft_lines<double2, false>(s_plane, plan.ax[0], plan.tw64[0], Ny, Nx, 1, false);
-    fft_lines<double2, false>(s_plane, plan.ax[1], plan.tw64[1], Nx, 1, Nx, true);
-    double2 *out = dst + band * n + off;
+    fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, Nx, 1, false);
+    fft_lines<V, false>(s_plane, tb.ax[1], tb.tw[1], Nx, 1, Nx, true);
+    V *out = dst + band * n + off;
     for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) out[i] = s_plane[i];
 }
 
 // ---- z pass with the per-G factor ------------------------------------------------
-__device__ __forceinline__ double tpa_k(double x) {
-    double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
-    return num / (num + 16.0 * x * x * x * x);
+template <typename T> __device__ __forceinline__ T tpa_k(T x) {
+    T num = (T)27 + x * ((T)18 + x * ((T)12 + (T)8 * x));
+    return num / (num + (T)16 * x * x * x * x);
 }
 
-template <Mid MID>
+template <typename V, Mid MID>
 __global__ void __launch_bounds__(FFT_THREADS)
-k_z_mid(Fft3Plan plan, double2 *__restrict__ buf, const double *__restrict__ tkin) {
-    extern __shared__ double2 s_slab[];
-    const int Nx = plan.ax[0].N, Ny = plan.ax[1].N, Nz = plan.ax[2].N;
+k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
+    using T = typename Sc<V>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *s_slab = reinterpret_cast<V *>(smem_raw);
+    const int Nx = tb.ax[0].N, Ny = tb.ax[1].N, Nz = tb.ax[2].N;
     const int y = blockIdx.x, band = blockIdx.y;
     const size_t n = (size_t)Nx * Ny * Nz;
     const size_t zstride = (size_t)Nx * Ny;
-    double2 *base = buf + band * n + (size_t)y * Nx;
+    V *base = buf + band * n + (size_t)y * Nx;
     const int tot = Nx * Nz;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
         int z = i / Nx, x = i - z * Nx;
         s_slab[i] = base[z * zstride + x];
     }
     __syncthreads();
-    fft_lines<double2, false>(s_slab, plan.ax[2], plan.tw64[2], Nx, 1, Nx, true);
-    const double inv_n = 1.0 / (double)n;
-    const double gy2 = plan.g2pos[1][y];
-    double tb = 1.0;
+    fft_lines<V, false>(s_slab, tb.ax[2], tb.tw[2], Nx, 1, Nx, true);
+    const T inv_n = (T)(1.0 / (double)n);
+    const T gy2 = tb.g2[1][y];
+    T tk = (T)1;
     if (MID == Mid::Tpa) {
-        tb = tkin[band];
-        if (!(tb >= 1e-12)) tb = 1.0;
+        double t = tkin[band];
+        if (!(t >= 1e-12)) t = 1.0;
+        tk = (T)t;
     }
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
         int z = i / Nx, x = i - z * Nx;
-        double g2 = plan.g2pos[0][x] + gy2 + plan.g2pos[2][z];
-        double f;
-        if (MID == Mid::Kinetic) f = 0.5 * g2 * inv_n;
-        else if (MID == Mid::Tpa) f = tpa_k(0.5 * g2 / tb) * inv_n;
-        else if (MID == Mid::Hartree) f = g2 > 0.0 ? 4.0 * M_PI / g2 * inv_n : 0.0;
+        T g2 = tb.g2[0][x] + gy2 + tb.g2[2][z];
+        T f;
+        if (MID == Mid::Kinetic) f = (T)0.5 * g2 * inv_n;
+        else if (MID == Mid::Tpa) f = tpa_k<T>((T)0.5 * g2 / tk) * inv_n;
+        else if (MID == Mid::Hartree) f = g2 > (T)0 ? (T)(4.0 * M_PI) / g2 * inv_n : (T)0;
         else f = inv_n;
-        s_slab[i] = make_double2(s_slab[i].x * f, s_slab[i].y * f);
+        s_slab[i] = mk<V>(s_slab[i].x * f, s_slab[i].y * f);
     }
     __syncthreads();
-    fft_lines<double2, true>(s_slab, plan.ax[2], plan.tw64[2], Nx, 1, Nx, true);
+    fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, 1, Nx, true);
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
         int z = i / Nx, x = i - z * Nx;
         base[z * zstride + x] = s_slab[i];
@@ -256,53 +293,55 @@ k_z_mid(Fft3Plan plan, double2 *__restrict__ buf, const double *__restrict__ tki
 // ---- xy inverse pass + epilogue ------------------------------------------------------
 enum class Epi { Plain, Hpsi, Real };
 
-template <Epi EPI>
+template <typename V, Epi EPI>
 __global__ void __launch_bounds__(FFT_THREADS)
-k_xy_inverse(Fft3Plan plan, const double2 *__restrict__ buf, const double2 *__restrict__ psi,
-             const double *__restrict__ v, ProjTables pt, const double2 *__restrict__ p,
-             double2 *__restrict__ out, double *__restrict__ rout) {
-    extern __shared__ double2 s_plane[];
-    const int Nx = plan.ax[0].N, Ny = plan.ax[1].N, Nz = plan.ax[2].N;
+k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi,
+             const typename Sc<V>::T *__restrict__ v, ProjT<typename Sc<V>::T> pt,
+             const V *__restrict__ p, V *__restrict__ out, double *__restrict__ rout) {
+    using T = typename Sc<V>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *s_plane = reinterpret_cast<V *>(smem_raw);
+    const int Nx = tb.ax[0].N, Ny = tb.ax[1].N, Nz = tb.ax[2].N;
     const int z = blockIdx.x, band = blockIdx.y;
     const size_t n = (size_t)Nx * Ny * Nz;
     const size_t plane = (size_t)Nx * Ny;
     const size_t off = (size_t)z * plane;
-    const double2 *in = buf + band * n + off;
+    const V *in = buf + band * n + off;
     for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = in[i];
     __syncthreads();
-    fft_lines<double2, true>(s_plane, plan.ax[1], plan.tw64[1], Nx, 1, Nx, true);
-    fft_lines<double2, true>(s_plane, plan.ax[0], plan.tw64[0], Ny, Nx, 1, false);
+    fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, 1, Nx, true);
+    fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, Nx, 1, false);
     if (EPI == Epi::Plain) {
-        double2 *o = out + band * n + off;
+        V *o = out + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = s_plane[i];
     } else if (EPI == Epi::Real) {
         double *o = rout + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = s_plane[i].x;
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = (double)s_plane[i].x;
     } else {
-        const double2 *ps = psi + band * n + off;
-        const double *vv = v + off;
+        const V *ps = psi + band * n + off;
+        const T *vv = v + off;
         const int np = pt.natom * pt.nproj;
-        const double2 *pb = p + (size_t)band * np;
-        double2 *o = out + band * n + off;
+        const V *pb = p + (size_t)band * np;
+        V *o = out + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
-            double2 t = s_plane[i];
-            double2 y = ps[i];
-            double vi = vv[i];
-            double ax = t.x + vi * y.x, ay = t.y + vi * y.y;
+            V t = s_plane[i];
+            V y = ps[i];
+            T vi = vv[i];
+            T ax = t.x + vi * y.x, ay = t.y + vi * y.y;
             const int g = (int)off + i;
             const int e0 = pt.c_rowptr[g], e1 = pt.c_rowptr[g + 1];
             for (int e = e0; e < e1; ++e) {
                 const int a = pt.c_atom[e];
-                const double *bt = pt.c_beta + 4 * (size_t)e;
+                const T *bt = pt.c_beta + 4 * (size_t)e;
                 for (int j = 0; j < pt.nproj; ++j) {
                     const int aj = a * pt.nproj + j;
-                    const double c = bt[j] * pt.e_kb[aj];
-                    const double2 q = pb[aj];
+                    const T c = bt[j] * pt.e_kb[aj];
+                    const V q = pb[aj];
                     ax += c * q.x;
                     ay += c * q.y;
                 }
             }
-            o[i] = make_double2(ax, ay);
+            o[i] = mk<V>(ax, ay);
         }
     }
 }
@@ -311,26 +350,28 @@ k_xy_inverse(Fft3Plan plan, const double2 *__restrict__ buf, const double2 *__re
 constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_BANDS = 4;
 
+template <typename V>
 __global__ void __launch_bounds__(PROJ_THREADS)
-k_project(ProjTables pt, const double2 *__restrict__ psi, double2 *__restrict__ p, int nb,
+k_project(ProjT<typename Sc<V>::T> pt, const V *__restrict__ psi, V *__restrict__ p, int nb,
           long long n, double dV) {
+    using T = typename Sc<V>::T;
     const int a = blockIdx.x;
     const int b0 = blockIdx.y * PROJ_BANDS;
     const int e0 = pt.a_start[a], e1 = pt.a_start[a + 1];
-    double acc[PROJ_BANDS][4][2];
+    T acc[PROJ_BANDS][4][2];
 #pragma unroll
     for (int bb = 0; bb < PROJ_BANDS; ++bb)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[bb][j][0] = acc[bb][j][1] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[bb][j][0] = acc[bb][j][1] = (T)0;
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int g = pt.a_idx[e];
-        const double *bt = pt.a_beta + 4 * (size_t)e;
-        const double be[4] = {bt[0], bt[1], bt[2], bt[3]};
+        const T *bt = pt.a_beta + 4 * (size_t)e;
+        const T be[4] = {bt[0], bt[1], bt[2], bt[3]};
 #pragma unroll
         for (int bb = 0; bb < PROJ_BANDS; ++bb) {
             const int band = b0 + bb;
             if (band >= nb) break;
-            const double2 v = psi[(size_t)band * n + g];
+            const V v = psi[(size_t)band * n + g];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 acc[bb][j][0] += be[j] * v.x;
@@ -339,7 +380,7 @@ k_project(ProjTables pt, const double2 *__restrict__ psi, double2 *__restrict__ 
         }
     }
     // block reduction, fixed order
-    __shared__ double red[PROJ_THREADS / 32][PROJ_BANDS * 8];
+    __shared__ T red[PROJ_THREADS / 32][PROJ_BANDS * 8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int bb = 0; bb < PROJ_BANDS; ++bb)
@@ -347,27 +388,36 @@ k_project(ProjTables pt, const double2 *__restrict__ psi, double2 *__restrict__ 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                double s = acc[bb][j][c];
+                T s = acc[bb][j][c];
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
                 if (lane == 0) red[warp][(bb * 4 + j) * 2 + c] = s;
             }
     __syncthreads();
     if (threadIdx.x < PROJ_BANDS * 8) {
-        double s = 0.0;
+        T s = (T)0;
         for (int w = 0; w < PROJ_THREADS / 32; ++w) s += red[w][threadIdx.x];
         const int bb = threadIdx.x / 8, j = (threadIdx.x / 2) % 4, c = threadIdx.x % 2;
         const int band = b0 + bb;
         if (band < nb && j < pt.nproj) {
-            double *dst = reinterpret_cast<double *>(p + (size_t)band * pt.natom * pt.nproj +
-                                                     a * pt.nproj + j);
-            dst[c] = s * dV;
+            T *dst = reinterpret_cast<T *>(p + (size_t)band * pt.natom * pt.nproj + a * pt.nproj + j);
+            dst[c] = s * (T)dV;
         }
     }
 }
 
+__global__ void k_to_float(const double *__restrict__ in, long long n, float *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 // ---- launchers -------------------------------------------------------------------------
-static size_t plane_bytes(const rsdft_ctx *ctx) { return (size_t)ctx->N[0] * ctx->N[1] * sizeof(double2); }
-static size_t slab_bytes(const rsdft_ctx *ctx) { return (size_t)ctx->N[0] * ctx->N[2] * sizeof(double2); }
+template <typename V> static size_t plane_bytes(const rsdft_ctx *ctx) {
+    return (size_t)ctx->N[0] * ctx->N[1] * sizeof(V);
+}
+template <typename V> static size_t slab_bytes(const rsdft_ctx *ctx) {
+    return (size_t)ctx->N[0] * ctx->N[2] * sizeof(V);
+}
 
 template <typename K> static rsdft_status set_smem(rsdft_ctx *ctx, K kernel, size_t bytes) {
     if (bytes > 48 * 1024)
@@ -375,94 +425,146 @@ template <typename K> static rsdft_status set_smem(rsdft_ctx *ctx, K kernel, siz
     return RSDFT_OK;
 }
 
-rsdft_status fft_xy_forward(rsdft_ctx *ctx, Src kind, const double2 *src, const double2 *src2,
-                            const double *theta, const int *act, const double *rsrc,
-                            double2 *dst, int nb, cudaStream_t st) {
+template <typename V>
+rsdft_status fft_xy_forward_t(rsdft_ctx *ctx, Src kind, const V *src, const V *src2,
+                              const double *theta, const int *act, const double *rsrc, V *dst,
+                              int nb, cudaStream_t st) {
     if (nb <= 0) return RSDFT_OK;
-    const size_t sm = plane_bytes(ctx);
+    const size_t sm = plane_bytes<V>(ctx);
     dim3 grid(ctx->N[2], nb);
     const double nxy = (double)ctx->N[0] * ctx->N[1];
-    const double bpp = kind == Src::Plain ? 32.0 : (kind == Src::Residual ? 48.0 : 24.0);
+    const double e = (double)sizeof(V);
+    const double bpp = kind == Src::Plain ? 2 * e : (kind == Src::Residual ? 3 * e : 8.0 + e);
     ProfScope ps(ctx, RSDFT_K_FFT_XY_FWD, 5.0 * nxy * std::log2(nxy) * ctx->N[2] * nb,
                  bpp * (double)ctx->n * nb, st);
+    const FftTabs<V> tb = tabs_of(ctx, (V *)nullptr);
     switch (kind) {
         case Src::Plain:
-            RS_TRY(set_smem(ctx, k_xy_forward<Src::Plain>, sm));
-            k_xy_forward<Src::Plain><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, src, src2, theta, act, rsrc, dst);
+            RS_TRY(set_smem(ctx, k_xy_forward<V, Src::Plain>, sm));
+            k_xy_forward<V, Src::Plain><<<grid, FFT_THREADS, sm, st>>>(tb, src, src2, theta, act, rsrc, dst);
             break;
         case Src::Residual:
-            RS_TRY(set_smem(ctx, k_xy_forward<Src::Residual>, sm));
-            k_xy_forward<Src::Residual><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, src, src2, theta, act, rsrc, dst);
+            RS_TRY(set_smem(ctx, k_xy_forward<V, Src::Residual>, sm));
+            k_xy_forward<V, Src::Residual><<<grid, FFT_THREADS, sm, st>>>(tb, src, src2, theta, act, rsrc, dst);
             break;
         case Src::RealField:
-            RS_TRY(set_smem(ctx, k_xy_forward<Src::RealField>, sm));
-            k_xy_forward<Src::RealField><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, src, src2, theta, act, rsrc, dst);
+            RS_TRY(set_smem(ctx, k_xy_forward<V, Src::RealField>, sm));
+            k_xy_forward<V, Src::RealField><<<grid, FFT_THREADS, sm, st>>>(tb, src, src2, theta, act, rsrc, dst);
             break;
     }
     RS_LAUNCHED(ctx, "k_xy_forward");
     return RSDFT_OK;
 }
 
-rsdft_status fft_z_mid(rsdft_ctx *ctx, Mid mid, double2 *buf, const double *tkin, int nb,
-                       cudaStream_t st) {
+template <typename V>
+rsdft_status fft_z_mid_t(rsdft_ctx *ctx, Mid mid, V *buf, const double *tkin, int nb,
+                         cudaStream_t st) {
     if (nb <= 0) return RSDFT_OK;
-    const size_t sm = slab_bytes(ctx);
+    const size_t sm = slab_bytes<V>(ctx);
     dim3 grid(ctx->N[1], nb);
     ProfScope ps(ctx, RSDFT_K_FFT_Z, 10.0 * (double)ctx->n * std::log2((double)ctx->N[2]) * nb,
-                 32.0 * (double)ctx->n * nb, st);
+                 2.0 * sizeof(V) * (double)ctx->n * nb, st);
+    const FftTabs<V> tb = tabs_of(ctx, (V *)nullptr);
     switch (mid) {
         case Mid::Kinetic:
-            RS_TRY(set_smem(ctx, k_z_mid<Mid::Kinetic>, sm));
-            k_z_mid<Mid::Kinetic><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, tkin);
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::Kinetic>, sm));
+            k_z_mid<V, Mid::Kinetic><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
             break;
         case Mid::Tpa:
-            RS_TRY(set_smem(ctx, k_z_mid<Mid::Tpa>, sm));
-            k_z_mid<Mid::Tpa><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, tkin);
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::Tpa>, sm));
+            k_z_mid<V, Mid::Tpa><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
             break;
         case Mid::Hartree:
-            RS_TRY(set_smem(ctx, k_z_mid<Mid::Hartree>, sm));
-            k_z_mid<Mid::Hartree><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, tkin);
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::Hartree>, sm));
+            k_z_mid<V, Mid::Hartree><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
             break;
         case Mid::Scale:
-            RS_TRY(set_smem(ctx, k_z_mid<Mid::Scale>, sm));
-            k_z_mid<Mid::Scale><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, tkin);
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::Scale>, sm));
+            k_z_mid<V, Mid::Scale><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
             break;
     }
     RS_LAUNCHED(ctx, "k_z_mid");
     return RSDFT_OK;
 }
 
-rsdft_status fft_xy_inverse(rsdft_ctx *ctx, const double2 *buf, const double2 *psi,
-                            const double2 *p, double2 *out, double *rout, int nb,
-                            cudaStream_t st) {
+template <typename V>
+rsdft_status fft_xy_inverse_t(rsdft_ctx *ctx, const V *buf, const V *psi, const V *p, V *out,
+                              double *rout, int nb, cudaStream_t st) {
     if (nb <= 0) return RSDFT_OK;
-    const size_t sm = plane_bytes(ctx);
+    const size_t sm = plane_bytes<V>(ctx);
     dim3 grid(ctx->N[2], nb);
     const double nxy = (double)ctx->N[0] * ctx->N[1];
-    const double bpp = rout ? 24.0 : (psi ? 48.0 : 32.0);
+    const double e = (double)sizeof(V);
+    const double bpp = rout ? e + 8.0 : (psi ? 3 * e : 2 * e);
     ProfScope ps(ctx, RSDFT_K_FFT_XY_INV, 5.0 * nxy * std::log2(nxy) * ctx->N[2] * nb,
-                 bpp * (double)ctx->n * nb + (psi ? 8.0 * (double)ctx->n : 0.0), st);
+                 bpp * (double)ctx->n * nb + (psi ? 0.5 * e * (double)ctx->n : 0.0), st);
+    const FftTabs<V> tb = tabs_of(ctx, (V *)nullptr);
+    const auto &pt = proj_of(ctx, (V *)nullptr);
+    const auto *v = v_of(ctx, (V *)nullptr);
     if (rout) {
-        RS_TRY(set_smem(ctx, k_xy_inverse<Epi::Real>, sm));
-        k_xy_inverse<Epi::Real><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, psi, ctx->v, ctx->pt, p, out, rout);
+        RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Real>, sm));
+        k_xy_inverse<V, Epi::Real><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
     } else if (psi) {
-        RS_TRY(set_smem(ctx, k_xy_inverse<Epi::Hpsi>, sm));
-        k_xy_inverse<Epi::Hpsi><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, psi, ctx->v, ctx->pt, p, out, rout);
+        RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Hpsi>, sm));
+        k_xy_inverse<V, Epi::Hpsi><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
     } else {
-        RS_TRY(set_smem(ctx, k_xy_inverse<Epi::Plain>, sm));
-        k_xy_inverse<Epi::Plain><<<grid, FFT_THREADS, sm, st>>>(ctx->fft, buf, psi, ctx->v, ctx->pt, p, out, rout);
+        RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Plain>, sm));
+        k_xy_inverse<V, Epi::Plain><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
     }
     RS_LAUNCHED(ctx, "k_xy_inverse");
     return RSDFT_OK;
 }
 
-rsdft_status project(rsdft_ctx *ctx, const double2 *psi, double2 *p, int nb, cudaStream_t st) {
+template <typename V>
+rsdft_status project_t(rsdft_ctx *ctx, const V *psi, V *p, int nb, cudaStream_t st) {
     if (nb <= 0 || ctx->pt.natom == 0) return RSDFT_OK;
     dim3 grid(ctx->pt.natom, cdiv(nb, PROJ_BANDS));
     const double ne = (double)ctx->nent;
-    ProfScope ps(ctx, RSDFT_K_PROJECT, 4.0 * ctx->pt.nproj * ne * nb, 16.0 * ne * nb + 36.0 * ne, st);
-    k_project<<<grid, PROJ_THREADS, 0, st>>>(ctx->pt, psi, p, nb, ctx->n, ctx->dV);
+    const double e = (double)sizeof(V);
+    ProfScope ps(ctx, RSDFT_K_PROJECT, 4.0 * ctx->pt.nproj * ne * nb, e * ne * nb + (4 + 2 * e) * ne, st);
+    k_project<V><<<grid, PROJ_THREADS, 0, st>>>(proj_of(ctx, (V *)nullptr), psi, p, nb, ctx->n, ctx->dV);
     RS_LAUNCHED(ctx, "k_project");
+    return RSDFT_OK;
+}
+
+rsdft_status fft_xy_forward(rsdft_ctx *ctx, Src kind, const double2 *src, const double2 *src2,
+                            const double *theta, const int *act, const double *rsrc,
+                            double2 *dst, int nb, cudaStream_t st) {
+    return fft_xy_forward_t<double2>(ctx, kind, src, src2, theta, act, rsrc, dst, nb, st);
+}
+rsdft_status fft_xy_forward32(rsdft_ctx *ctx, Src kind, const float2 *src, const float2 *src2,
+                              const double *theta, const int *act, float2 *dst, int nb,
+                              cudaStream_t st) {
+    return fft_xy_forward_t<float2>(ctx, kind, src, src2, theta, act, nullptr, dst, nb, st);
+}
+rsdft_status fft_z_mid(rsdft_ctx *ctx, Mid mid, double2 *buf, const double *tkin, int nb,
+                       cudaStream_t st) {
+    return fft_z_mid_t<double2>(ctx, mid, buf, tkin, nb, st);
+}
+rsdft_status fft_z_mid32(rsdft_ctx *ctx, Mid mid, float2 *buf, const double *tkin, int nb,
+                         cudaStream_t st) {
+    return fft_z_mid_t<float2>(ctx, mid, buf, tkin, nb, st);
+}
+rsdft_status fft_xy_inverse(rsdft_ctx *ctx, const double2 *buf, const double2 *psi,
+                            const double2 *p, double2 *out, double *rout, int nb,
+                            cudaStream_t st) {
+    return fft_xy_inverse_t<double2>(ctx, buf, psi, p, out, rout, nb, st);
+}
+rsdft_status fft_xy_inverse32(rsdft_ctx *ctx, const float2 *buf, const float2 *psi,
+                              const float2 *p, float2 *out, int nb, cudaStream_t st) {
+    return fft_xy_inverse_t<float2>(ctx, buf, psi, p, out, nullptr, nb, st);
+}
+rsdft_status project(rsdft_ctx *ctx, const double2 *psi, double2 *p, int nb, cudaStream_t st) {
+    return project_t<double2>(ctx, psi, p, nb, st);
+}
+rsdft_status project32(rsdft_ctx *ctx, const float2 *psi, float2 *p, int nb, cudaStream_t st) {
+    return project_t<float2>(ctx, psi, p, nb, st);
+}
+
+rsdft_status refresh_v32(rsdft_ctx *ctx, cudaStream_t st) {
+    k_to_float<<<std::max(1, std::min(cdiv(ctx->n, 256), 608)), 256, 0, st>>>(ctx->v, ctx->n, ctx->v32);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_to_float");
     return RSDFT_OK;
 }
 
@@ -473,6 +575,19 @@ rsdft_status apply_h64(rsdft_ctx *ctx, const double2 *psi, double2 *hpsi, int nb
     RS_TRY(fft_xy_forward(ctx, Src::Plain, psi, nullptr, nullptr, nullptr, nullptr, ctx->ws.T1, nb, st));
     RS_TRY(fft_z_mid(ctx, Mid::Kinetic, ctx->ws.T1, nullptr, nb, st));
     RS_TRY(fft_xy_inverse(ctx, ctx->ws.T1, psi, ctx->ws.proj, hpsi, nullptr, nb, st));
+    return RSDFT_OK;
+}
+
+// FP32 H psi; the FP32 copy of V must be current (refresh_v32).
+rsdft_status apply_h32(rsdft_ctx *ctx, const float2 *psi, float2 *hpsi, int nb, cudaStream_t st) {
+    if (nb <= 0) return RSDFT_OK;
+    RS_TRY(ensure_workspace(ctx, nb));
+    float2 *proj = reinterpret_cast<float2 *>(ctx->ws.proj);
+    float2 *t1 = reinterpret_cast<float2 *>(ctx->ws.T1);
+    RS_TRY(project32(ctx, psi, proj, nb, st));
+    RS_TRY(fft_xy_forward32(ctx, Src::Plain, psi, nullptr, nullptr, nullptr, t1, nb, st));
+    RS_TRY(fft_z_mid32(ctx, Mid::Kinetic, t1, nullptr, nb, st));
+    RS_TRY(fft_xy_inverse32(ctx, t1, psi, proj, hpsi, nb, st));
     return RSDFT_OK;
 }
 
@@ -488,7 +603,11 @@ rsdft_status rsdft_apply_h(rsdft_ctx *ctx, const void *psi_dev, void *hpsi_dev, 
     if (nband < 0 || (nband > 0 && (!psi_dev || !hpsi_dev)))
         return fail(ctx, RSDFT_E_INVALID, "bad psi/hpsi/nband");
     if (psi_dev == hpsi_dev && nband > 0) return fail(ctx, RSDFT_E_INVALID, "psi and hpsi must not overlap");
-    if (prec != RSDFT_FP64) return fail(ctx, RSDFT_E_INVALID, "only RSDFT_FP64 is available");
+    if (prec == RSDFT_MIXED) {
+        RS_TRY(refresh_v32(ctx, as_stream(stream)));
+        return apply_h32(ctx, (const float2 *)psi_dev, (float2 *)hpsi_dev, nband, as_stream(stream));
+    }
+    if (prec != RSDFT_FP64) return fail(ctx, RSDFT_E_INVALID, "unknown precision");
     return apply_h64(ctx, (const double2 *)psi_dev, (double2 *)hpsi_dev, nband, as_stream(stream));
 }
 

@@ -14,7 +14,8 @@ constexpr int GT = 64;      // output tile edge
 constexpr int GKC = 16;     // reduction chunk per shared-memory stage
 constexpr int GTHREADS = 256;
 
-__device__ __forceinline__ const double2 *row_of(const RowBlocks &rb, int i, long long n) {
+template <typename V>
+__device__ __forceinline__ const V *row_of(const RowBlocksT<V> &rb, int i, long long n) {
     if (i < rb.cnt[0]) return rb.ptr[0] + (size_t)i * n;
     i -= rb.cnt[0];
     if (i < rb.cnt[1]) return rb.ptr[1] + (size_t)i * n;
@@ -30,53 +31,60 @@ __device__ __forceinline__ void upper_tile(int t, int T, int &ti, int &tj) {
     tj = i + t;
 }
 
+// Partial tiles of G over one K-chunk.  V = double2 (FP64) or float2 (the
+// mixed form: FP32 products and accumulation inside the CTA); the partials are
+// stored in FP64 and reduced in FP64 by k_gram_reduce.  Output tile edge 16*P
+// (each of the 16 x 16 threads owns P x P entries).
+template <typename V, int P>
 __global__ void __launch_bounds__(GTHREADS)
-k_gram_partial(RowBlocks A, RowBlocks B, int na, int nb, long long n, int hermitian, int Ti,
+k_gram_partial(RowBlocksT<V> A, RowBlocksT<V> B, int na, int nb, long long n, int hermitian, int Ti,
                int Tj, long long kchunk, double2 *__restrict__ part) {
-    __shared__ double2 As[GKC][GT + 1];
-    __shared__ double2 Bs[GKC][GT + 1];
+    using T = decltype(V{}.x);
+    constexpr int TE = 16 * P;
+    __shared__ V As[GKC][TE + 1];
+    __shared__ V Bs[GKC][TE + 1];
     int ti, tj;
     if (hermitian) upper_tile(blockIdx.x, Ti, ti, tj);
     else { ti = blockIdx.x / Tj; tj = blockIdx.x % Tj; }
     const int split = blockIdx.y;
     const long long k0 = (long long)split * kchunk;
     const long long k1 = min(n, k0 + kchunk);
-    const int i0 = ti * GT, j0 = tj * GT;
+    const int i0 = ti * TE, j0 = tj * TE;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double ar[4][4], ai[4][4];
+    T ar[P][P], ai[P][P];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < P; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.0;
-    // loader mapping: 64 rows x 16 k per stage, 4 elements per thread
-    const int lrow = threadIdx.x >> 2, lk = (threadIdx.x & 3) * 4;
-    const double2 *arow = (i0 + lrow < na) ? row_of(A, i0 + lrow, n) : nullptr;
-    const double2 *brow = (j0 + lrow < nb) ? row_of(B, j0 + lrow, n) : nullptr;
+        for (int b = 0; b < P; ++b) ar[a][b] = ai[a][b] = (T)0;
+    // loader: TE rows x 16 k per stage; 16 consecutive threads read one row's chunk
     for (long long kb = k0; kb < k1; kb += GKC) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const long long kk = kb + lk + q;
-            double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+        for (int q = 0; q < P; ++q) {
+            const int idx = threadIdx.x + q * GTHREADS;
+            const int lrow = idx >> 4, lk = idx & 15;
+            const long long kk = kb + lk;
+            V va, vb;
+            va.x = va.y = vb.x = vb.y = (T)0;
             if (kk < k1) {
-                if (arow) va = arow[kk];
-                if (brow) vb = brow[kk];
+                if (i0 + lrow < na) va = row_of(A, i0 + lrow, n)[kk];
+                if (j0 + lrow < nb) vb = row_of(B, j0 + lrow, n)[kk];
             }
-            As[lk + q][lrow] = va;
-            Bs[lk + q][lrow] = vb;
+            As[lk][lrow] = va;
+            Bs[lk][lrow] = vb;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < GKC; ++k) {
-            double2 a[4], b[4];
+            V a[P], b[P];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < P; ++q) {
                 a[q] = As[k][ty + 16 * q];
                 b[q] = Bs[k][tx + 16 * q];
             }
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+            for (int p = 0; p < P; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < P; ++q) {
                     // conj(a) * b
                     ar[p][q] = fma(a[p].x, b[q].x, fma(a[p].y, b[q].y, ar[p][q]));
                     ai[p][q] = fma(a[p].x, b[q].y, fma(-a[p].y, b[q].x, ai[p][q]));
@@ -86,19 +94,19 @@ k_gram_partial(RowBlocks A, RowBlocks B, int na, int nb, long long n, int hermit
     }
     double2 *pp = part + (size_t)split * na * nb;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < P; ++p) {
         const int i = i0 + ty + 16 * p;
         if (i >= na) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < P; ++q) {
             const int j = j0 + tx + 16 * q;
-            if (j < nb) pp[(size_t)i * nb + j] = make_double2(ar[p][q], ai[p][q]);
+            if (j < nb) pp[(size_t)i * nb + j] = make_double2((double)ar[p][q], (double)ai[p][q]);
         }
     }
 }
 
 __global__ void k_gram_reduce(const double2 *__restrict__ part, int nsplit, int na, int nb,
-                              int hermitian, double scale, double2 *__restrict__ g, int ldg) {
+                              int hermitian, int te, double scale, double2 *__restrict__ g, int ldg) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)na * nb) return;
     const int i = (int)(idx / nb), j = (int)(idx % nb);
@@ -116,7 +124,7 @@ __global__ void k_gram_reduce(const double2 *__restrict__ part, int nsplit, int 
     if (!hermitian) {
         val = sum_at(i, j);
     } else {
-        const int ti = i / GT, tj = j / GT;
+        const int ti = i / te, tj = j / te;
         if (ti < tj) val = sum_at(i, j);
         else if (ti > tj) { double2 t = sum_at(j, i); val = make_double2(t.x, -t.y); }
         else {
@@ -142,19 +150,55 @@ static rsdft_status ensure_gram_part(rsdft_ctx *ctx, size_t elems) {
     return RSDFT_OK;
 }
 
-rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
-                  bool hermitian, double scale, cudaStream_t st) {
-    const int na = A.cnt[0] + A.cnt[1] + A.cnt[2];
-    const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
-    if (na <= 0 || nb <= 0) return RSDFT_OK;
-    if (hermitian && na != nb) return fail(ctx, RSDFT_E_INVALID, "hermitian gram needs na == nb");
-    const int Ti = cdiv(na, GT), Tj = cdiv(nb, GT);
+// Resident CTAs of a kernel per SM (queried once per instantiation).
+template <typename K> static int occupancy(K kernel, int threads) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return std::max(1, occ);
+}
+
+// Output tile edge 16*P with the least padding over an extent (ties: larger P).
+static int pick_p(int extent_a, int extent_b) {
+    int best = 4;
+    long long bestpad = -1;
+    for (int P = 4; P >= 2; --P) {
+        const long long te = 16 * P;
+        const long long pad = (long long)cdiv(extent_a, te) * te * cdiv(extent_b, te) * te;
+        if (bestpad < 0 || pad < bestpad) { bestpad = pad; best = P; }
+    }
+    return best;
+}
+
+// Split count for `tiles` output tiles: the first count whose grid fills whole
+// waves of the resident-CTA capacity to 97% (else the best seen), keeping at
+// least 512 reduction points per CTA.
+static int pick_splits(int tiles, long long n, int capacity) {
+    int best = 1;
+    double besteff = 0.0;
+    for (int ns = 1; ns <= 128; ++ns) {
+        if (ns > 1 && n / ns < 512) break;
+        const long long ctas = (long long)tiles * ns;
+        const long long waves = (ctas + capacity - 1) / capacity;
+        const double eff = (double)ctas / (double)(waves * capacity);
+        if (eff > besteff + 1e-9) { besteff = eff; best = ns; }
+        if (eff >= 0.97) return ns;
+    }
+    return best;
+}
+
+template <typename V, int P>
+static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B,
+                                int na, int nb, double2 *g, int ldg, bool hermitian, double scale,
+                                cudaStream_t st) {
+    constexpr int TE = 16 * P;
+    static int occ = occupancy(k_gram_partial<V, P>, GTHREADS);
+    const int Ti = cdiv(na, TE), Tj = cdiv(nb, TE);
     const int tiles = hermitian ? Ti * (Ti + 1) / 2 : Ti * Tj;
     const long long n = ctx->n;
-    // split the reduction so that the grid fills the GPU a few times over
-    int nsplit = cdiv(1216, tiles);
-    nsplit = std::max(1, std::min(nsplit, 16));
-    while (nsplit > 1 && n / nsplit < 2048) --nsplit;
+    int nsplit = pick_splits(tiles, n, ctx->num_sms * occ);
     long long kchunk = (n + nsplit - 1) / nsplit;
     kchunk = (kchunk + GKC - 1) / GKC * GKC;
     nsplit = (int)((n + kchunk - 1) / kchunk);
@@ -164,69 +208,99 @@ rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double
         const bool same = A.ptr[0] == B.ptr[0] && A.ptr[1] == B.ptr[1] && A.ptr[2] == B.ptr[2];
         const double entries = hermitian ? 0.5 * na * (na + 1.0) : (double)na * nb;
         ProfScope ps(ctx, RSDFT_K_GRAM, 8.0 * (double)n * entries,
-                     16.0 * (double)n * (same ? na : na + nb), st);
-        k_gram_partial<<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj, kchunk,
-                                                  ctx->ws.gram_part);
+                     (double)sizeof(V) * (double)n * (same ? na : na + nb), st);
+        k_gram_partial<V, P><<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj,
+                                                        kchunk, ctx->ws.gram_part);
     }
     RS_LAUNCHED(ctx, "k_gram_partial");
     const long long tot = (long long)na * nb;
     k_gram_reduce<<<cdiv(tot, 256), 256, 0, st>>>(ctx->ws.gram_part, nsplit, na, nb,
-                                                   hermitian ? 1 : 0, scale, g, ldg);
+                                                   hermitian ? 1 : 0, TE, scale, g, ldg);
     count_launch(ctx);
     RS_LAUNCHED(ctx, "k_gram_reduce");
     return RSDFT_OK;
+}
+
+template <typename V>
+rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B, double2 *g, int ldg,
+                    bool hermitian, double scale, cudaStream_t st) {
+    const int na = A.cnt[0] + A.cnt[1] + A.cnt[2];
+    const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
+    if (na <= 0 || nb <= 0) return RSDFT_OK;
+    if (hermitian && na != nb) return fail(ctx, RSDFT_E_INVALID, "hermitian gram needs na == nb");
+    switch (pick_p(na, nb)) {
+        case 2: return gram_launch<V, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+        case 3: return gram_launch<V, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+        default: return gram_launch<V, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+    }
+}
+
+rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
+                  bool hermitian, double scale, cudaStream_t st) {
+    return gram_t<double2>(ctx, A, B, g, ldg, hermitian, scale, st);
+}
+rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
+                    double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st) {
+    return gram_t<float2>(ctx, A, B, g, ldg, hermitian, scale, st);
 }
 
 // ---- rotation ----------------------------------------------------------------------
 // Tile: 64 bands x 64 points.  Rows of Y are consumed block 1, block 2, then
 // block 0, so that out1 (the W/P part alone) is available before the X part is
 // added.
+template <typename V, int PB>
 __global__ void __launch_bounds__(GTHREADS)
-k_rotate(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long long n,
-         const double2 *base, int sign, double2 *out0, double2 *out1) {
-    __shared__ double2 Cs[GKC][GT + 1];
-    __shared__ double2 Ys[GKC][GT + 1];
-    const int b0 = blockIdx.x * GT;
+k_rotate(RowBlocksT<V> Y, const double2 *__restrict__ c, int ldc, int m, long long n,
+         const V *base, int sign, V *out0, V *out1) {
+    using T = decltype(V{}.x);
+    constexpr int TB = 16 * PB;   // bands per tile (the points per tile are GT = 64)
+    __shared__ V Cs[GKC][TB + 1];
+    __shared__ V Ys[GKC][GT + 1];
+    const int b0 = blockIdx.x * TB;
     const long long r0 = (long long)blockIdx.y * GT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double accx[4][4], accy[4][4];
+    T accx[PB][4], accy[PB][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < PB; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) accx[p][q] = accy[p][q] = 0.0;
-    const int order[3] = {1, 2, 0};
-    int rowstart[3];
-    rowstart[0] = 0;
-    rowstart[1] = Y.cnt[0];
-    rowstart[2] = Y.cnt[0] + Y.cnt[1];
+        for (int q = 0; q < 4; ++q) accx[p][q] = accy[p][q] = (T)0;
+#pragma unroll
     for (int oi = 0; oi < 3; ++oi) {
-        const int blk = order[oi];
-        const int cnt = Y.cnt[blk];
-        const double2 *yb = Y.ptr[blk];
-        const int crow0 = rowstart[blk];
+        // blocks in the order 1, 2, 0; crow0 = first row of the block in c
+        const int cnt = oi == 0 ? Y.cnt[1] : (oi == 1 ? Y.cnt[2] : Y.cnt[0]);
+        const V *yb = oi == 0 ? Y.ptr[1] : (oi == 1 ? Y.ptr[2] : Y.ptr[0]);
+        const int crow0 = oi == 0 ? Y.cnt[0] : (oi == 1 ? Y.cnt[0] + Y.cnt[1] : 0);
         for (int kb = 0; kb < cnt; kb += GKC) {
             for (int idx = threadIdx.x; idx < GKC * GT; idx += GTHREADS) {
                 const int kk = idx / GT, cc = idx % GT;
                 const int i = kb + kk;
-                double2 cv = make_double2(0.0, 0.0), yv = make_double2(0.0, 0.0);
-                if (i < cnt) {
-                    if (b0 + cc < m) cv = c[(size_t)(crow0 + i) * ldc + b0 + cc];
-                    if (r0 + cc < n) yv = yb[(size_t)i * n + r0 + cc];
+                V yv;
+                yv.x = yv.y = (T)0;
+                if (i < cnt && r0 + cc < n) yv = yb[(size_t)i * n + r0 + cc];
+                Ys[kk][cc] = yv;
+            }
+            for (int idx = threadIdx.x; idx < GKC * TB; idx += GTHREADS) {
+                const int kk = idx / TB, cc = idx % TB;
+                const int i = kb + kk;
+                V cv;
+                cv.x = cv.y = (T)0;
+                if (i < cnt && b0 + cc < m) {
+                    const double2 cd = c[(size_t)(crow0 + i) * ldc + b0 + cc];
+                    cv.x = (T)cd.x;
+                    cv.y = (T)cd.y;
                 }
                 Cs[kk][cc] = cv;
-                Ys[kk][cc] = yv;
             }
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < GKC; ++k) {
-                double2 cv[4], yv[4];
+                V cv[PB], yv[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    cv[q] = Cs[k][ty + 16 * q];
-                    yv[q] = Ys[k][tx + 16 * q];
-                }
+                for (int q = 0; q < PB; ++q) cv[q] = Cs[k][ty + 16 * q];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
+                for (int q = 0; q < 4; ++q) yv[q] = Ys[k][tx + 16 * q];
+#pragma unroll
+                for (int p = 0; p < PB; ++p)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         accx[p][q] = fma(cv[p].x, yv[q].x, fma(-cv[p].y, yv[q].y, accx[p][q]));
@@ -237,48 +311,83 @@ k_rotate(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long long n
         }
         if (oi == 1 && out1) {
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
+            for (int p = 0; p < PB; ++p) {
                 const int b = b0 + ty + 16 * p;
                 if (b >= m) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const long long r = r0 + tx + 16 * q;
-                    if (r < n) out1[(size_t)b * n + r] = make_double2(accx[p][q], accy[p][q]);
+                    if (r < n) {
+                        V o;
+                        o.x = accx[p][q];
+                        o.y = accy[p][q];
+                        out1[(size_t)b * n + r] = o;
+                    }
                 }
             }
         }
     }
-    const double sg = (double)sign;
+    const T sg = (T)sign;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < PB; ++p) {
         const int b = b0 + ty + 16 * p;
         if (b >= m) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const long long r = r0 + tx + 16 * q;
             if (r >= n) continue;
-            double ox = sg * accx[p][q], oy = sg * accy[p][q];
+            T ox = sg * accx[p][q], oy = sg * accy[p][q];
             if (base) {
-                const double2 bv = base[(size_t)b * n + r];
+                const V bv = base[(size_t)b * n + r];
                 ox += bv.x;
                 oy += bv.y;
             }
-            out0[(size_t)b * n + r] = make_double2(ox, oy);
+            V o;
+            o.x = ox;
+            o.y = oy;
+            out0[(size_t)b * n + r] = o;
         }
+    }
+}
+
+template <typename V, int PB>
+static rsdft_status rotate_launch(rsdft_ctx *ctx, const RowBlocksT<V> &Y, const double2 *c, int ldc,
+                                  int m, const V *base, int sign, V *out0, V *out1, cudaStream_t st) {
+    dim3 grid(cdiv(m, 16 * PB), cdiv(ctx->n, GT));
+    const int k = Y.cnt[0] + Y.cnt[1] + Y.cnt[2];
+    ProfScope ps(ctx, RSDFT_K_ROTATE, 8.0 * (double)ctx->n * k * m,
+                 (double)sizeof(V) * (double)ctx->n * (k + m + (out1 ? m : 0) + (base ? m : 0)), st);
+    k_rotate<V, PB><<<grid, GTHREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base, sign, out0, out1);
+    RS_LAUNCHED(ctx, "k_rotate");
+    return RSDFT_OK;
+}
+
+// Band tile 16*PB with the least padding over m bands (ties: larger PB).
+template <typename V>
+rsdft_status rotate_t(rsdft_ctx *ctx, const RowBlocksT<V> &Y, const double2 *c, int ldc, int m,
+                      const V *base, int sign, V *out0, V *out1, cudaStream_t st) {
+    if (m <= 0) return RSDFT_OK;
+    int best = 4, bestpad = 1 << 30;
+    for (int pb = 4; pb >= 1; --pb) {
+        const int pad = cdiv(m, 16 * pb) * 16 * pb - m;
+        if (pad < bestpad) { bestpad = pad; best = pb; }
+    }
+    switch (best) {
+        case 1: return rotate_launch<V, 1>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+        case 2: return rotate_launch<V, 2>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+        case 3: return rotate_launch<V, 3>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+        default: return rotate_launch<V, 4>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
     }
 }
 
 rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ldc, int m,
                     const double2 *base, int sign, double2 *out0, double2 *out1,
                     cudaStream_t st) {
-    if (m <= 0) return RSDFT_OK;
-    dim3 grid(cdiv(m, GT), cdiv(ctx->n, GT));
-    const int k = Y.cnt[0] + Y.cnt[1] + Y.cnt[2];
-    ProfScope ps(ctx, RSDFT_K_ROTATE, 8.0 * (double)ctx->n * k * m,
-                 16.0 * (double)ctx->n * (k + m + (out1 ? m : 0) + (base ? m : 0)), st);
-    k_rotate<<<grid, GTHREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base, sign, out0, out1);
-    RS_LAUNCHED(ctx, "k_rotate");
-    return RSDFT_OK;
+    return rotate_t<double2>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+}
+rsdft_status rotate32(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const double2 *c, int ldc, int m,
+                      const float2 *base, int sign, float2 *out0, float2 *out1, cudaStream_t st) {
+    return rotate_t<float2>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
 }
 
 // ---- Gram without allocation -------------------------------------------------------
@@ -347,10 +456,10 @@ rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int
     RowBlocks B{{(const double2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
     // every partial entry the reduction reads is written by this launch first,
     // so nothing left by an earlier call is read
-    k_gram_partial<<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
+    k_gram_partial<double2, 4><<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_partial: %s", cudaGetErrorString(e));
-    k_gram_reduce<<<cdiv((long long)na * nb, 256), 256, 0, st>>>(part, nsplit, na, nb, 0, scale,
+    k_gram_reduce<<<cdiv((long long)na * nb, 256), 256, 0, st>>>(part, nsplit, na, nb, 0, GT, scale,
                                                                  (double2 *)g_dev, nb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_reduce: %s", cudaGetErrorString(e));

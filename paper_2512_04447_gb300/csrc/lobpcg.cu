@@ -16,6 +16,7 @@
 namespace rsdft {
 
 constexpr int RTHREADS = 256;
+constexpr double PIVOT_TOL_FP32 = 1e-5;
 
 __device__ __forceinline__ double block_sum2(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -32,20 +33,22 @@ __device__ __forceinline__ double block_sum2(double v, double *sh) {
     return sh[32];
 }
 
-// res[b] = ||hx_b - theta_b x_b|| (dV metric); vexp[b] = <x_b|V|x_b>
+// res[b] = ||hx_b - theta_b x_b|| (dV metric, FP64 sums); vexp[b] = <x_b|V|x_b>
+template <typename V>
 __global__ void __launch_bounds__(RTHREADS)
-k_resid(const double2 *__restrict__ hx, const double2 *__restrict__ x, const double *__restrict__ theta,
+k_resid(const V *__restrict__ hx, const V *__restrict__ x, const double *__restrict__ theta,
         const double *__restrict__ v, long long n, double dV, double *res, double *vexp) {
     __shared__ double sh[33];
     const int b = blockIdx.x;
     const double th = theta[b];
-    const double2 *h = hx + (size_t)b * n, *xx = x + (size_t)b * n;
+    const V *h = hx + (size_t)b * n, *xx = x + (size_t)b * n;
     double s = 0.0, sv = 0.0;
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const double2 a = h[i], c = xx[i];
-        const double rx = a.x - th * c.x, ry = a.y - th * c.y;
+        const V a = h[i], c = xx[i];
+        const double cx = (double)c.x, cy = (double)c.y;
+        const double rx = (double)a.x - th * cx, ry = (double)a.y - th * cy;
         s += rx * rx + ry * ry;
-        sv += v[i] * (c.x * c.x + c.y * c.y);
+        sv += v[i] * (cx * cx + cy * cy);
     }
     s = block_sum2(s, sh);
     sv = block_sum2(sv, sh);
@@ -57,8 +60,9 @@ k_resid(const double2 *__restrict__ hx, const double2 *__restrict__ x, const dou
 
 // t_b = <x_b|T|x_b> = theta_b - <x_b|V|x_b> - sum_aj E_aj |<beta_aj|x_b>|^2, for the
 // active bands (compact index j).
+template <typename V>
 __global__ void k_tkin(const double *__restrict__ theta, const double *__restrict__ vexp,
-                       const double2 *__restrict__ p, ProjTables pt, const int *__restrict__ act,
+                       const V *__restrict__ p, ProjTables pt, const int *__restrict__ act,
                        int na, double *tkin) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= na) return;
@@ -66,34 +70,40 @@ __global__ void k_tkin(const double *__restrict__ theta, const double *__restric
     const int np = pt.natom * pt.nproj;
     double nl = 0.0;
     for (int q = 0; q < np; ++q) {
-        const double2 c = p[(size_t)b * np + q];
-        nl += pt.e_kb[q] * (c.x * c.x + c.y * c.y);
+        const V c = p[(size_t)b * np + q];
+        nl += pt.e_kb[q] * ((double)c.x * c.x + (double)c.y * c.y);
     }
     tkin[j] = theta[b] - vexp[b] - nl;
 }
 
+template <typename V>
 __global__ void __launch_bounds__(RTHREADS)
-k_rownorm(const double2 *__restrict__ a, long long n, double dV, double *out) {
+k_rownorm(const V *__restrict__ a, long long n, double dV, double *out) {
     __shared__ double sh[33];
     const int b = blockIdx.x;
-    const double2 *r = a + (size_t)b * n;
+    const V *r = a + (size_t)b * n;
     double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += r[i].x * r[i].x + r[i].y * r[i].y;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = r[i].x, y = r[i].y;
+        s += x * x + y * y;
+    }
     s = block_sum2(s, sh);
     if (threadIdx.x == 0) out[b] = sqrt(s * dV);
 }
 
 // a[b] /= nrm[b] and (optionally) a2[b] /= nrm[b]
-__global__ void k_scale_rows(double2 *a, double2 *a2, long long n, const double *__restrict__ nrm) {
+template <typename V>
+__global__ void k_scale_rows(V *a, V *a2, long long n, const double *__restrict__ nrm) {
+    using T = decltype(V{}.x);
     const int b = blockIdx.y;
-    const double s = 1.0 / nrm[b];
+    const T s = (T)(1.0 / nrm[b]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double2 &x = a[(size_t)b * n + i];
+        V &x = a[(size_t)b * n + i];
         x.x *= s;
         x.y *= s;
         if (a2) {
-            double2 &y = a2[(size_t)b * n + i];
+            V &y = a2[(size_t)b * n + i];
             y.x *= s;
             y.y *= s;
         }
@@ -101,9 +111,10 @@ __global__ void k_scale_rows(double2 *a, double2 *a2, long long n, const double 
 }
 
 // dst[j] = src[act[j]] (and dst2/src2 alike)
-__global__ void k_gather_rows(const double2 *__restrict__ src, const double2 *__restrict__ src2,
-                              const int *__restrict__ act, long long n, double2 *__restrict__ dst,
-                              double2 *__restrict__ dst2) {
+template <typename V>
+__global__ void k_gather_rows(const V *__restrict__ src, const V *__restrict__ src2,
+                              const int *__restrict__ act, long long n, V *__restrict__ dst,
+                              V *__restrict__ dst2) {
     const int j = blockIdx.y;
     const int b = act[j];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -114,34 +125,91 @@ __global__ void k_gather_rows(const double2 *__restrict__ src, const double2 *__
 }
 
 // w[j] = hx[act[j]] - theta[act[j]] x[act[j]]
-__global__ void k_residual_rows(const double2 *__restrict__ hx, const double2 *__restrict__ x,
+template <typename V>
+__global__ void k_residual_rows(const V *__restrict__ hx, const V *__restrict__ x,
                                 const double *__restrict__ theta, const int *__restrict__ act,
-                                long long n, double2 *__restrict__ w) {
+                                long long n, V *__restrict__ w) {
+    using T = decltype(V{}.x);
     const int j = blockIdx.y;
     const int b = act[j];
-    const double th = theta[b];
+    const T th = (T)theta[b];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double2 h = hx[(size_t)b * n + i], c = x[(size_t)b * n + i];
-        w[(size_t)j * n + i] = make_double2(h.x - th * c.x, h.y - th * c.y);
+        const V h = hx[(size_t)b * n + i], c = x[(size_t)b * n + i];
+        V o;
+        o.x = h.x - th * c.x;
+        o.y = h.y - th * c.y;
+        w[(size_t)j * n + i] = o;
     }
 }
 
-rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st) {
-    if (nb <= 0) return RSDFT_OK;
-    k_rownorm<<<nb, RTHREADS, 0, st>>>(a, ctx->n, ctx->dV, out);
-    count_launch(ctx);
-    RS_LAUNCHED(ctx, "k_rownorm");
-    return RSDFT_OK;
+template <typename A, typename B>
+__global__ void k_convert(const A *__restrict__ in, long long cnt, B *__restrict__ out) {
+    using T = decltype(B{}.x);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        B o;
+        o.x = (T)in[i].x;
+        o.y = (T)in[i].y;
+        out[i] = o;
+    }
 }
 
-static rsdft_status scale_rows(rsdft_ctx *ctx, double2 *a, double2 *a2, int nb, const double *nrm,
+// Precision dispatch of the building blocks.
+template <typename V> struct Ops;
+template <> struct Ops<double2> {
+    static rsdft_status apply_h(rsdft_ctx *c, const double2 *x, double2 *h, int nb, cudaStream_t st) {
+        return apply_h64(c, x, h, nb, st);
+    }
+    static rsdft_status project(rsdft_ctx *c, const double2 *x, double2 *p, int nb, cudaStream_t st) {
+        return rsdft::project(c, x, p, nb, st);
+    }
+    static rsdft_status tpa(rsdft_ctx *c, const double2 *hx, const double2 *x, const double *th,
+                            const int *act, const double *tk, double2 *t1, double2 *w, int na,
+                            cudaStream_t st) {
+        RS_TRY(fft_xy_forward(c, Src::Residual, hx, x, th, act, nullptr, t1, na, st));
+        RS_TRY(fft_z_mid(c, Mid::Tpa, t1, tk, na, st));
+        return fft_xy_inverse(c, t1, nullptr, nullptr, w, nullptr, na, st);
+    }
+    static rsdft_status gram(rsdft_ctx *c, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
+                             bool herm, double sc, cudaStream_t st) {
+        return rsdft::gram(c, A, B, g, ldg, herm, sc, st);
+    }
+    static rsdft_status rotate(rsdft_ctx *c, const RowBlocks &Y, const double2 *cf, int ldc, int m,
+                               const double2 *base, int sign, double2 *o0, double2 *o1, cudaStream_t st) {
+        return rsdft::rotate(c, Y, cf, ldc, m, base, sign, o0, o1, st);
+    }
+};
+template <> struct Ops<float2> {
+    static rsdft_status apply_h(rsdft_ctx *c, const float2 *x, float2 *h, int nb, cudaStream_t st) {
+        return apply_h32(c, x, h, nb, st);
+    }
+    static rsdft_status project(rsdft_ctx *c, const float2 *x, float2 *p, int nb, cudaStream_t st) {
+        return project32(c, x, p, nb, st);
+    }
+    static rsdft_status tpa(rsdft_ctx *c, const float2 *hx, const float2 *x, const double *th,
+                            const int *act, const double *tk, float2 *t1, float2 *w, int na,
+                            cudaStream_t st) {
+        RS_TRY(fft_xy_forward32(c, Src::Residual, hx, x, th, act, t1, na, st));
+        RS_TRY(fft_z_mid32(c, Mid::Tpa, t1, tk, na, st));
+        return fft_xy_inverse32(c, t1, nullptr, nullptr, w, na, st);
+    }
+    static rsdft_status gram(rsdft_ctx *c, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
+                             double2 *g, int ldg, bool herm, double sc, cudaStream_t st) {
+        return gram32(c, A, B, g, ldg, herm, sc, st);
+    }
+    static rsdft_status rotate(rsdft_ctx *c, const RowBlocksT<float2> &Y, const double2 *cf, int ldc,
+                               int m, const float2 *base, int sign, float2 *o0, float2 *o1,
                                cudaStream_t st) {
+        return rotate32(c, Y, cf, ldc, m, base, sign, o0, o1, st);
+    }
+};
+
+rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st) {
     if (nb <= 0) return RSDFT_OK;
-    dim3 g(std::min(cdiv(ctx->n, 256), 1024), nb);
-    k_scale_rows<<<g, 256, 0, st>>>(a, a2, ctx->n, nrm);
+    k_rownorm<double2><<<nb, RTHREADS, 0, st>>>(a, ctx->n, ctx->dV, out);
     count_launch(ctx);
-    RS_LAUNCHED(ctx, "k_scale_rows");
+    RS_LAUNCHED(ctx, "k_rownorm");
     return RSDFT_OK;
 }
 
@@ -174,40 +242,58 @@ struct PhaseEvents {
     }
 };
 
-static rsdft_status lobpcg64(rsdft_ctx *ctx, double2 *x_user, int m, const rsdft_lobpcg_opts &o,
-                             double *eig_host, double *res_host, rsdft_lobpcg_stats *stats,
-                             cudaStream_t st) {
-    RS_TRY(ensure_workspace(ctx, m));
+struct RunState {
+    int iterations = 0;
+    int dropped = 0;
+    bool converged = false;   // max residual over nconv <= stop_tol
+};
+
+// One LOBPCG run in precision V on the workspace.  x_in / x_out: [m][n] V.
+// Stops when the max residual over the first nconv bands is <= stop_tol, after
+// maxit iterations, when every band is soft-locked, or (stagnation = true)
+// when the max residual fell by less than 10% in each of 3 iterations.
+template <typename V>
+static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
+                             const rsdft_lobpcg_opts &o, double stop_tol, int maxit, bool stagnation,
+                             RunState &rs, double *hres, rsdft_lobpcg_stats *stats, cudaStream_t st) {
+    using Blocks = RowBlocksT<V>;
     Workspace &w = ctx->ws;
     const long long n = ctx->n;
     const double dV = ctx->dV;
     const int nconv = (o.nconv <= 0 || o.nconv > m) ? m : o.nconv;
-    double2 *X = w.X, *HX = w.HX, *Xn = w.Xn, *HXn = w.HXn;
-    double *hres = w.hbuf;                    // [m]
-    int *hact = reinterpret_cast<int *>(w.hbuf + m);   // [m]
-    RS_CUDA(ctx, cudaMemcpyAsync(X, x_user, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    RS_TRY(apply_h64(ctx, X, HX, m, st));
-    // initial Rayleigh-Ritz on span(X)
+    V *X = (V *)w.X, *HX = (V *)w.HX, *Xn = (V *)w.Xn, *HXn = (V *)w.HXn;
+    V *W = (V *)w.W, *HW = (V *)w.HW, *P = (V *)w.P, *HP = (V *)w.HP;
+    V *Pn = (V *)w.Pn, *HPn = (V *)w.HPn, *T1 = (V *)w.T1;
+    V *proj = (V *)w.proj;
+    int *hact = reinterpret_cast<int *>(w.hbuf + m);
+    // Gram matrices formed from FP32 orbitals carry relative errors ~1e-7, so
+    // a pivot below 1e-5 of the largest diagonal is noise there: the FP32 data
+    // path drops such columns (the FP64 path keeps the caller's floor).
+    const double pivot_tol = sizeof(V) == sizeof(float2) ? std::max(o.pivot_tol, PIVOT_TOL_FP32)
+                                                         : o.pivot_tol;
+    if ((const void *)x_in != (const void *)X)
+        RS_CUDA(ctx, cudaMemcpyAsync(X, x_in, (size_t)m * n * sizeof(V), cudaMemcpyDeviceToDevice, st));
+    RS_TRY(Ops<V>::apply_h(ctx, X, HX, m, st));
     {
-        RowBlocks Y{{X, nullptr, nullptr}, {m, 0, 0}};
-        RowBlocks HY{{HX, nullptr, nullptr}, {m, 0, 0}};
-        RS_TRY(gram(ctx, Y, Y, w.GS, m, true, dV, st));
-        RS_TRY(gram(ctx, Y, HY, w.GH, m, true, dV, st));
+        Blocks Y{{X, nullptr, nullptr}, {m, 0, 0}};
+        Blocks HY{{HX, nullptr, nullptr}, {m, 0, 0}};
+        RS_TRY(Ops<V>::gram(ctx, Y, Y, w.GS, m, true, dV, st));
+        RS_TRY(Ops<V>::gram(ctx, Y, HY, w.GH, m, true, dV, st));
         int nd = 0;
-        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, o.pivot_tol, w.theta, w.Cfull, &nd, st));
-        RS_TRY(rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
-        RS_TRY(rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, pivot_tol, w.theta, w.Cfull, &nd, st));
+        RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
+        RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
         std::swap(X, Xn);
         std::swap(HX, HXn);
     }
     PhaseEvents pe;
     if (stats) RS_TRY(pe.init(ctx));
     bool haveP = false;
-    int it = 0, dropped = 0;
-    bool converged = false;
+    int it = 0, slow = 0;
+    double prev = -1.0;
     rsdft_status result = RSDFT_OK;
     for (;;) {
-        k_resid<<<m, RTHREADS, 0, st>>>(HX, X, w.theta, ctx->v, n, dV, w.res, w.vexp);
+        k_resid<V><<<m, RTHREADS, 0, st>>>(HX, X, w.theta, ctx->v, n, dV, w.res, w.vexp);
         count_launch(ctx);
         RS_LAUNCHED(ctx, "k_resid");
         RS_CUDA(ctx, cudaMemcpyAsync(hres, w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -220,8 +306,13 @@ static rsdft_status lobpcg64(rsdft_ctx *ctx, double2 *x_user, int m, const rsdft
             if (b < nconv) rmax = std::max(rmax, hres[b]);
         }
         if (bad) { result = fail(ctx, RSDFT_E_NUMERIC, "non-finite residual at iteration %d", it); break; }
-        converged = rmax <= o.tol;
-        if (converged || it >= o.maxit) break;
+        rs.converged = rmax <= stop_tol;
+        if (rs.converged || it >= maxit) break;
+        if (stagnation && prev > 0.0) {
+            slow = rmax > 0.9 * prev ? slow + 1 : 0;
+            if (slow >= 3) break;
+        }
+        prev = rmax;
         int na = 0;
         for (int b = 0; b < m; ++b)
             if (hres[b] > o.lock_tol) hact[na++] = b;
@@ -229,55 +320,54 @@ static rsdft_status lobpcg64(rsdft_ctx *ctx, double2 *x_user, int m, const rsdft
         RS_CUDA(ctx, cudaMemcpyAsync(w.act, hact, na * sizeof(int), cudaMemcpyHostToDevice, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[0], st));
         // ---- preconditioned residuals W (compact over the active bands)
-        RS_TRY(project(ctx, X, w.proj, m, st));
-        k_tkin<<<cdiv(na, 128), 128, 0, st>>>(w.theta, w.vexp, w.proj, ctx->pt, w.act, na, w.tkin);
-        count_launch(ctx);
-        RS_LAUNCHED(ctx, "k_tkin");
+        const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
         if (o.precond == RSDFT_PRECOND_TPA) {
-            RS_TRY(fft_xy_forward(ctx, Src::Residual, HX, X, w.theta, w.act, nullptr, w.T1, na, st));
-            RS_TRY(fft_z_mid(ctx, Mid::Tpa, w.T1, w.tkin, na, st));
-            RS_TRY(fft_xy_inverse(ctx, w.T1, nullptr, nullptr, w.W, nullptr, na, st));
+            RS_TRY(Ops<V>::project(ctx, X, proj, m, st));
+            k_tkin<V><<<cdiv(na, 128), 128, 0, st>>>(w.theta, w.vexp, proj, ctx->pt, w.act, na, w.tkin);
+            count_launch(ctx);
+            RS_LAUNCHED(ctx, "k_tkin");
+            RS_TRY(Ops<V>::tpa(ctx, HX, X, w.theta, w.act, w.tkin, T1, W, na, st));
         } else {
-            dim3 g(std::min(cdiv(n, 256), 1024), na);
-            k_residual_rows<<<g, 256, 0, st>>>(HX, X, w.theta, w.act, n, w.W);
+            k_residual_rows<V><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, W);
             count_launch(ctx);
             RS_LAUNCHED(ctx, "k_residual_rows");
         }
         // W <- W - X <X|W>
         {
-            RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
-            RowBlocks YW{{w.W, nullptr, nullptr}, {na, 0, 0}};
-            RS_TRY(gram(ctx, YX, YW, w.C, na, false, dV, st));
-            RS_TRY(rotate(ctx, YX, w.C, na, na, w.W, -1, w.W, nullptr, st));
+            Blocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
+            Blocks YW{{W, nullptr, nullptr}, {na, 0, 0}};
+            RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
+            RS_TRY(Ops<V>::rotate(ctx, YX, w.C, na, na, W, -1, W, nullptr, st));
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[1], st));
-        RS_TRY(apply_h64(ctx, w.W, w.HW, na, st));
+        RS_TRY(Ops<V>::apply_h(ctx, W, HW, na, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[2], st));
-        RS_TRY(colnorms(ctx, w.W, na, w.nrm, st));
-        RS_TRY(scale_rows(ctx, w.W, w.HW, na, w.nrm, st));
+        k_rownorm<V><<<na, RTHREADS, 0, st>>>(W, n, dV, w.nrm);
+        k_scale_rows<V><<<rowgrid, 256, 0, st>>>(W, HW, n, w.nrm);
+        count_launch(ctx, 2);
+        RS_LAUNCHED(ctx, "normalise W");
         int np_ = 0;
         if (haveP) {
-            dim3 g(std::min(cdiv(n, 256), 1024), na);
-            k_gather_rows<<<g, 256, 0, st>>>(w.P, w.HP, w.act, n, w.Pn, w.HPn);
-            count_launch(ctx);
-            RS_LAUNCHED(ctx, "k_gather_rows");
-            RS_TRY(colnorms(ctx, w.Pn, na, w.nrm, st));
-            RS_TRY(scale_rows(ctx, w.Pn, w.HPn, na, w.nrm, st));
+            k_gather_rows<V><<<rowgrid, 256, 0, st>>>(P, HP, w.act, n, Pn, HPn);
+            k_rownorm<V><<<na, RTHREADS, 0, st>>>(Pn, n, dV, w.nrm);
+            k_scale_rows<V><<<rowgrid, 256, 0, st>>>(Pn, HPn, n, w.nrm);
+            count_launch(ctx, 3);
+            RS_LAUNCHED(ctx, "normalise P");
             np_ = na;
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[3], st));
         const int k = m + na + np_;
-        RowBlocks Y{{X, w.W, w.Pn}, {m, na, np_}};
-        RowBlocks HY{{HX, w.HW, w.HPn}, {m, na, np_}};
-        RS_TRY(gram(ctx, Y, Y, w.GS, k, true, dV, st));
-        RS_TRY(gram(ctx, Y, HY, w.GH, k, true, dV, st));
+        Blocks Y{{X, W, Pn}, {m, na, np_}};
+        Blocks HY{{HX, HW, HPn}, {m, na, np_}};
+        RS_TRY(Ops<V>::gram(ctx, Y, Y, w.GS, k, true, dV, st));
+        RS_TRY(Ops<V>::gram(ctx, Y, HY, w.GH, k, true, dV, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
         int nd = 0;
-        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, o.pivot_tol, w.lam, w.Cfull, &nd, st));
-        dropped += nd;
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
+        rs.dropped += nd;
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[5], st));
-        RS_TRY(rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, w.P, st));
-        RS_TRY(rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, w.HP, st));
+        RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, P, st));
+        RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, HP, st));
         if (stats) {
             RS_CUDA(ctx, cudaEventRecord(pe.ev[6], st));
             pe.pending = true;
@@ -292,24 +382,61 @@ static rsdft_status lobpcg64(rsdft_ctx *ctx, double2 *x_user, int m, const rsdft
         RS_CUDA(ctx, cudaStreamSynchronize(st));
         pe.collect(stats);
         pe.destroy();
-        stats->iterations = it;
-        stats->converged = converged ? 1 : 0;
-        stats->dropped = dropped;
     }
+    rs.iterations += it;
     // keep the workspace pointers consistent with the swaps
-    w.X = X; w.Xn = Xn; w.HX = HX; w.HXn = HXn;
-    RS_CUDA(ctx, cudaMemcpyAsync(x_user, X, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    if (eig_host) RS_CUDA(ctx, cudaMemcpyAsync(eig_host, w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RS_CUDA(ctx, cudaStreamSynchronize(st));
-    if (res_host) memcpy(res_host, hres, m * sizeof(double));
-    if (result != RSDFT_OK) return result;
-    return converged || o.tol <= 0.0 ? RSDFT_OK : RSDFT_E_NOT_CONVERGED;
+    w.X = (double2 *)X; w.Xn = (double2 *)Xn; w.HX = (double2 *)HX; w.HXn = (double2 *)HXn;
+    if ((void *)x_out != (void *)X)
+        RS_CUDA(ctx, cudaMemcpyAsync(x_out, X, (size_t)m * n * sizeof(V), cudaMemcpyDeviceToDevice, st));
+    return result;
 }
 
 rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_opts &o,
                         double *eig_host, double *res_host, rsdft_lobpcg_stats *stats,
                         cudaStream_t st) {
-    return lobpcg64(ctx, x, m, o, eig_host, res_host, stats, st);
+    RS_TRY(ensure_workspace(ctx, m));
+    Workspace &w = ctx->ws;
+    double *hres = w.hbuf;
+    RunState rs;
+    int it_mixed = 0;
+    rsdft_status r = RSDFT_OK;
+    if (o.precision == RSDFT_MIXED) {
+        // mixed form: FP32 data path until switch_tol (or stagnation), then FP64
+        RS_TRY(refresh_v32(ctx, st));
+        float2 *xs = w.Xs;
+        const long long cnt = (long long)m * ctx->n;
+        k_convert<double2, float2><<<std::min(cdiv(cnt, 256), 4096), 256, 0, st>>>(x, cnt, xs);
+        count_launch(ctx);
+        RS_LAUNCHED(ctx, "k_convert");
+        const double stop = std::max(o.tol, o.switch_tol);
+        r = lobpcg_t<float2>(ctx, xs, xs, m, o, stop, o.maxit, o.tol > 0.0, rs, hres, stats, st);
+        if (r != RSDFT_OK) return r;
+        it_mixed = rs.iterations;
+        k_convert<float2, double2><<<std::min(cdiv(cnt, 256), 4096), 256, 0, st>>>(xs, cnt, x);
+        count_launch(ctx);
+        RS_LAUNCHED(ctx, "k_convert");
+        if (o.tol > 0.0 || rs.iterations < o.maxit) {
+            RunState r2;
+            const int left = o.tol > 0.0 ? std::max(0, o.maxit - rs.iterations) : o.maxit - rs.iterations;
+            r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
+            rs.iterations += r2.iterations;
+            rs.dropped += r2.dropped;
+            rs.converged = r2.converged;
+        }
+    } else {
+        r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, o.maxit, false, rs, hres, stats, st);
+    }
+    if (stats) {
+        stats->iterations = rs.iterations;
+        stats->iterations_mixed = it_mixed;
+        stats->converged = rs.converged ? 1 : 0;
+        stats->dropped = rs.dropped;
+    }
+    if (eig_host) RS_CUDA(ctx, cudaMemcpyAsync(eig_host, w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(ctx, cudaStreamSynchronize(st));
+    if (res_host) memcpy(res_host, hres, m * sizeof(double));
+    if (r != RSDFT_OK) return r;
+    return rs.converged || o.tol <= 0.0 ? RSDFT_OK : RSDFT_E_NOT_CONVERGED;
 }
 
 }  // namespace rsdft
@@ -327,6 +454,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->precision = RSDFT_FP64;
     o->lock_tol = 1e-10;
     o->pivot_tol = 1e-8;
+    o->switch_tol = 1e-4;
 }
 
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
@@ -338,9 +466,11 @@ rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lo
     rsdft_lobpcg_opts o;
     rsdft_lobpcg_default_opts(&o);
     if (opts) o = *opts;
-    if (o.maxit < 0 || !(o.tol >= 0.0) || !(o.pivot_tol >= 0.0) || !(o.lock_tol >= 0.0))
+    if (o.maxit < 0 || !(o.tol >= 0.0) || !(o.pivot_tol >= 0.0) || !(o.lock_tol >= 0.0) ||
+        !(o.switch_tol >= 0.0))
         return fail(ctx, RSDFT_E_INVALID, "bad LOBPCG options");
-    if (o.precision != RSDFT_FP64) return fail(ctx, RSDFT_E_INVALID, "only RSDFT_FP64 is available");
+    if (o.precision != RSDFT_FP64 && o.precision != RSDFT_MIXED)
+        return fail(ctx, RSDFT_E_INVALID, "unknown precision");
     if (o.precond != RSDFT_PRECOND_TPA && o.precond != RSDFT_PRECOND_NONE)
         return fail(ctx, RSDFT_E_INVALID, "unknown preconditioner");
     if (stats) *stats = rsdft_lobpcg_stats{};

@@ -32,19 +32,22 @@ struct Fft3Plan {
     const double2 *tw64[3];  // [N] exp(-2 pi i k / N), device
     const float2 *tw32[3];
     const double *g2pos[3];  // G_a^2 at each digit-reversed position, device
+    const float *g2pos32[3];
 };
 
-// Device views handed to kernels.
-struct ProjTables {
+// Device views handed to kernels (T = double for the FP64 form, float for the
+// FP32 data path of the mixed form; the index arrays are shared).
+template <typename T> struct ProjT {
     int natom, nproj;
     const int *a_start;      // [natom+1] atom-major entry ranges
     const int *a_idx;        // [nent] grid index
-    const double *a_beta;    // [nent][4] beta values (unused slots 0)
+    const T *a_beta;         // [nent][4] beta values (unused slots 0)
     const int *c_rowptr;     // [n+1] point-major CSR
     const int *c_atom;       // [nent]
-    const double *c_beta;    // [nent][4]
-    const double *e_kb;      // [natom*nproj]
+    const T *c_beta;         // [nent][4]
+    const T *e_kb;           // [natom*nproj]
 };
+using ProjTables = ProjT<double>;
 
 struct Workspace {
     int cap_band = 0;        // bands the buffers are sized for
@@ -52,6 +55,7 @@ struct Workspace {
     double2 *X = nullptr, *HX = nullptr, *W = nullptr, *HW = nullptr, *P = nullptr,
             *HP = nullptr, *T1 = nullptr, *Xn = nullptr, *HXn = nullptr, *Pn = nullptr,
             *HPn = nullptr;
+    float2 *Xs = nullptr;    // FP32 orbital block of the mixed form [cap_band][n]
     // projector coefficients [cap_band][natom*nproj]
     double2 *proj = nullptr;
     // subspace: k = 3 * cap_band
@@ -100,11 +104,14 @@ struct rsdft_ctx {
     double L[3];
     long long n;
     double dV;
+    int num_sms = 1;                 // SMs of the device the context was made on
     rsdft::Fft3Plan fft;
     std::vector<void *> owned;       // device allocations freed at destroy
     double *vloc = nullptr;          // [n] the V_loc given at create
     double *v = nullptr;             // [n] potential used by H
+    float *v32 = nullptr;            // [n] FP32 copy of v for the mixed form
     rsdft::ProjTables pt{};
+    rsdft::ProjT<float> pt32{};
     long long nent = 0;
     rsdft::Workspace ws;
     rsdft::ScfWork scf;
@@ -173,12 +180,24 @@ rsdft_status fft_xy_inverse(rsdft_ctx *ctx, const double2 *buf, const double2 *p
 rsdft_status project(rsdft_ctx *ctx, const double2 *psi, double2 *p, int nb, cudaStream_t st);
 rsdft_status apply_h64(rsdft_ctx *ctx, const double2 *psi, double2 *hpsi, int nb,
                        cudaStream_t st);
+// FP32 data path of the mixed form
+rsdft_status fft_xy_forward32(rsdft_ctx *ctx, Src kind, const float2 *src, const float2 *src2,
+                              const double *theta, const int *act, float2 *dst, int nb,
+                              cudaStream_t st);
+rsdft_status fft_z_mid32(rsdft_ctx *ctx, Mid mid, float2 *buf, const double *tkin, int nb,
+                         cudaStream_t st);
+rsdft_status fft_xy_inverse32(rsdft_ctx *ctx, const float2 *buf, const float2 *psi,
+                              const float2 *p, float2 *out, int nb, cudaStream_t st);
+rsdft_status project32(rsdft_ctx *ctx, const float2 *psi, float2 *p, int nb, cudaStream_t st);
+rsdft_status apply_h32(rsdft_ctx *ctx, const float2 *psi, float2 *hpsi, int nb, cudaStream_t st);
+rsdft_status refresh_v32(rsdft_ctx *ctx, cudaStream_t st);
 
 // ---- GEMM-shaped kernels (gemm.cu) -------------------------------------------
-struct RowBlocks {
-    const double2 *ptr[3];
+template <typename V> struct RowBlocksT {
+    const V *ptr[3];
     int cnt[3];
 };
+using RowBlocks = RowBlocksT<double2>;
 // g[i][j] = scale * sum_r conj(A_i) B_j over rows of A (na) and B (nb).
 // hermitian: A and B index the same basis; only tiles with ti <= tj are formed
 // and g is completed as a Hermitian matrix.  ldg = leading dimension of g.
@@ -189,6 +208,12 @@ rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double
 rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ldc, int m,
                     const double2 *base, int sign, double2 *out0, double2 *out1,
                     cudaStream_t st);
+// FP32 operands (mixed form): products and CTA-level sums in FP32, Gram
+// partials reduced in FP64; rotation coefficients rounded to FP32.
+rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
+                    double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st);
+rsdft_status rotate32(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const double2 *c, int ldc, int m,
+                      const float2 *base, int sign, float2 *out0, float2 *out1, cudaStream_t st);
 
 // ---- dense core (dense.cu) ----------------------------------------------------
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,

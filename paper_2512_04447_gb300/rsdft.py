@@ -48,11 +48,13 @@ class Projectors(C.Structure):
 
 class LobpcgOpts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("tol", C.c_double), ("nconv", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double)]
+                ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double),
+                ("switch_tol", C.c_double)]
 
 
 class LobpcgStats(C.Structure):
-    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("dropped", C.c_int),
+    _fields_ = [("iterations", C.c_int), ("iterations_mixed", C.c_int), ("converged", C.c_int),
+                ("dropped", C.c_int),
                 ("ms_hpsi", C.c_double), ("ms_precond", C.c_double), ("ms_gram", C.c_double),
                 ("ms_dense", C.c_double), ("ms_rotate", C.c_double), ("ms_other", C.c_double)]
 
@@ -63,7 +65,7 @@ class LobpcgStats(C.Structure):
 class ScfOpts(C.Structure):
     _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("beta", C.c_double),
                 ("depth", C.c_int), ("k_lobpcg", C.c_int), ("first_maxit", C.c_int),
-                ("tol", C.c_double), ("precond", C.c_int)]
+                ("tol", C.c_double), ("precond", C.c_int), ("precision", C.c_int)]
 
 
 class ScfOut(C.Structure):
