@@ -183,7 +183,17 @@ def kernel_roofline(name, d, precision, sm_mhz, hbm_gbs):
     s = d["ms"] / 1e3
     if s <= 0 or d["launches"] == 0:
         return None
-    fp32 = precision == "mixed"
+    fp32 = precision != "fp64"
+    if name == "gram_tc":
+        # split-BF16 x3 on tcgen05: three BF16 MMAs per product, against the
+        # measured dense BF16 tensor peak
+        s_ = d["ms"] / 1e3
+        ach = d["flops"] / s_ / 1e12
+        peak = float(_peaks().get("bf16_tflops", 1955.4))
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "avg_launch_ms": s_ / d["launches"] * 1e3,
+                "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS BF16 GEMM, burst)"}
     alu = name in ("gram", "rotate") or (name.startswith("fft") and not fp32)
     per_launch_s = s / d["launches"]
     if alu:
@@ -204,9 +214,10 @@ def kernel_roofline(name, d, precision, sm_mhz, hbm_gbs):
 
 def time_form(ctx, R, torch, x0, wl, precision, args, barrier, stream):
     """First (converged) SCF step, warm-up, then the timed steps of one form."""
-    prec = R.MIXED if precision == "mixed" else R.FP64
+    prec = R.FP64 if precision == "fp64" else R.MIXED
     opts = ctx.scf_opts(n_electrons=wl.n_electrons, kT=wl.kT, beta=0.3, depth=4, k_lobpcg=3,
-                        first_maxit=200, tol=1e-6, precision=prec)
+                        first_maxit=200, tol=1e-6, precision=prec,
+                        tensor_cores=1 if precision == "mixed_tc" else 0)
     x = torch.from_numpy(x0).cuda()
     ctx.scf_init(wl.nband, opts)
     barrier()
@@ -258,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    forms = ["fp64", "mixed", "mixed_tc"] if args.precision == "all" else [args.precision]
     head = forms[-1]            # the form the headline value is quoted on
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -305,10 +316,12 @@ def run_ours(args, rank, world, local_rank):
                       "first_step_lobpcg_iterations": r["first_iters"],
                       "gpu_launches": r["launches"], "kernels": kern,
                       "scf_last": {k: r["outs"][-1][k] for k in ("e_tot", "drho", "step")}}
-    if "fp64" in res and "mixed" in res:
+    if "fp64" in res:
         import numpy as np
-        summary["mixed"]["first_step_eig_max_abs_diff_vs_fp64"] = float(
-            np.max(np.abs(res["mixed"]["eig0"] - res["fp64"]["eig0"])))
+        for f in forms:
+            if f != "fp64":
+                summary[f]["first_step_eig_max_abs_diff_vs_fp64"] = float(
+                    np.max(np.abs(res[f]["eig0"] - res["fp64"]["eig0"])))
     # dominant single kernel of the headline form (the dense core is a group of launches)
     hk = {k: v for k, v in summary[head]["kernels"].items() if k != "dense"}
     dom = max(hk, key=lambda k: hk[k]["ms_total"])
@@ -319,14 +332,18 @@ def run_ours(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed_tc": "bf16x3+f32+f64"}[head],
+            "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: 64 C diamond (2x2x2, a=6.74, L=13.48 bohr), 64^3 "
                                    "grid, 144 bands (128 occupied), Gaussian V_loc Z=4 sigma=0.6, "
                                    "4 KB projectors/atom, LDA + FFT Hartree + Anderson(0.3, depth 4); "
                                    "step = SCF step with 3 LOBPCG iterations",
-                       "precision": ("mixed: FP32 orbitals for H psi/FFT/Gram/rotation, FP64 norms "
-                                     "and dense core; first solve refined in FP64 to 1e-6 Ha"
-                                     if head == "mixed" else "FP64 throughout"),
+                       "precision": {"fp64": "FP64 throughout",
+                                     "mixed": "mixed: FP32 orbitals for H psi/FFT/Gram/rotation, "
+                                              "FP64 norms and dense core; first solve refined in "
+                                              "FP64 to 1e-6 Ha",
+                                     "mixed_tc": "mixed as above with the Gram matrices as "
+                                                 "split-BF16 x3 tcgen05 GEMMs (FP32 accumulation)"}[head],
                        "learned_preconditioner": "not built (TPA in both forms)",
                        "l2": "inputs larger than L2 (orbital block 604 MB vs 129 MB L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -359,7 +376,12 @@ def run_profile_case(case):
     ctx = R.Context((10.11,) * 3, N, np.zeros(N[0] * N[1] * N[2]))
     g = torch.Generator(device="cuda").manual_seed(0)
     cdt = torch.complex64 if case.endswith("32") else torch.complex128
-    if case.startswith("gram") or case.startswith("rotate"):
+    if case == "gram_tc":
+        # split-BF16 tensor-core Gram of a 432-row FP32 block (382 MB)
+        y = torch.randn(432, ctx.n, dtype=torch.complex64, device="cuda", generator=g)
+        gm = torch.empty(432, 432, dtype=torch.complex128, device="cuda")
+        ctx.gram_bf16x3(y, y, gm)
+    elif case.startswith("gram") or case.startswith("rotate"):
         y = torch.randn(432, ctx.n, dtype=torch.complex128, device="cuda", generator=g)
         if case.startswith("gram"):
             gm = torch.empty(432, 432, dtype=torch.complex128, device="cuda")
@@ -385,9 +407,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed", "mixed_tc"])
     ap.add_argument("--profile-case", default=None,
-                    help="run one small case for ncu (gram, rotate, hpsi, hpsi32) and exit")
+                    help="run one small case for ncu (gram, gram_tc, rotate, hpsi, hpsi32) and exit")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)

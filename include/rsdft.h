@@ -158,6 +158,15 @@ rsdft_status rsdft_gram(rsdft_ctx *ctx, const void *a_dev, int na, const void *b
 rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int nb, long long n,
                                double scale, void *g_dev, void *stream);
 
+/* Gram matrix of complex64 blocks on the tensor cores (the mixed form):
+ * G[i][j] = dV sum_r conj(a_i(r)) b_j(r) with each FP32 value split into
+ * bf16 hi + lo and the products hi*hi + hi*lo + lo*hi accumulated in FP32 on
+ * tcgen05 (TMEM), FP32 partials over K blocks summed in FP64 (SCF task (2),
+ * mixed precision).  a_dev: [na][n], b_dev: [nb][n] complex64; g_dev: [na][nb]
+ * complex128.  Relative error about 1e-5 of max |G|. */
+rsdft_status rsdft_gram_bf16x3(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
+                               void *g_dev, void *stream);
+
 /* Rotation out[b] = sum_i c[i][b] y[i] (+ base[b] when base_dev != NULL;
  * base may alias out).  y_dev: [k][n]; c_dev: [k][m] row-major;
  * out_dev, base_dev: [m][n]; complex128.  sign = +1 adds, -1 subtracts the sum. */
@@ -199,11 +208,15 @@ typedef struct {
     int precision;         /* rsdft_precision                                      */
     double lock_tol;       /* soft-lock bands with residual <= lock_tol (1e-10)    */
     double pivot_tol;      /* relative Cholesky pivot floor for G_S (1e-8; the FP32
-                              data path of RSDFT_MIXED uses at least 1e-5)        */
+                              data path of RSDFT_MIXED uses at least 1e-3 and soft-
+                              locks bands at residual <= 1e-6)                    */
     double switch_tol;     /* RSDFT_MIXED: FP32 data path until the max residual
                               is <= max(tol, switch_tol) (1e-4) or stagnates (3
                               iterations gaining < 10%), then FP64 to tol; 0 runs
                               FP32 iterations to maxit                            */
+    int tensor_cores;      /* RSDFT_MIXED: 1 forms the Gram matrices of the FP32
+                              phase with split-BF16 tcgen05 GEMMs, 0 with FP32
+                              CUDA cores (default 0)                              */
 } rsdft_lobpcg_opts;
 
 typedef struct {
@@ -241,6 +254,7 @@ typedef struct {
                               first solve in the mixed form (FP32 data path to
                               1e-4, then FP64 to tol) and the later steps' k_lobpcg
                               iterations on the FP32 data path                    */
+    int tensor_cores;      /* as rsdft_lobpcg_opts.tensor_cores                    */
 } rsdft_scf_opts;
 
 typedef struct {
@@ -292,7 +306,8 @@ typedef enum {
     RSDFT_K_FFT_XY_INV = 4,  /* xy-plane inverse pass (+ V psi + projectors)    */
     RSDFT_K_PROJECT = 5,     /* projector gather <beta|psi>                     */
     RSDFT_K_DENSE = 6,       /* Cholesky, TRSM, eigensolve of the subspace      */
-    RSDFT_K_COUNT = 7
+    RSDFT_K_GRAM_TC = 7,     /* tensor-core split-BF16 Gram (tcgen05)           */
+    RSDFT_K_COUNT = 8
 } rsdft_kernel_id;
 
 rsdft_status rsdft_profile_enable(rsdft_ctx *ctx, int on);

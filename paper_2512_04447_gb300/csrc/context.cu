@@ -246,7 +246,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     };
     void *olds[] = {w.X, w.HX, w.W, w.HW, w.P, w.HP, w.T1, w.Xn, w.HXn, w.Pn, w.HPn, w.Xs, w.proj,
                     w.GS, w.GH, w.C, w.Cfull, w.gram_part, w.Lm, w.Km, w.Ym, w.Vh, w.Zc,
-                    w.tau, w.wv, w.d, w.e, w.lam, w.zt, w.dscr, w.fac, w.drop, w.keep, w.ikeep,
+                    w.tau, w.wv, w.d, w.e, w.lam, w.zt, w.dscr, w.fac, w.gsync, w.drop, w.keep, w.ikeep,
                     w.theta, w.res, w.vexp, w.tkin, w.nrm, w.act};
     for (void *p : olds) release(p);
     if (w.hbuf) cudaFreeHost(w.hbuf);
@@ -271,11 +271,12 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     RS_TRY(dev_alloc(ctx, (void **)&w.zt, k * k * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.dscr, (8 * k + 64) * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.fac, 5 * k * k * sizeof(double)));
+    RS_TRY(dev_alloc(ctx, (void **)&w.gsync, 64));
     for (int **b : {&w.drop, &w.keep, &w.ikeep})
         RS_TRY(dev_alloc(ctx, (void **)b, (k + 1) * sizeof(int)));
     for (double **b : {&w.theta, &w.res, &w.vexp, &w.tkin, &w.nrm})
         RS_TRY(dev_alloc(ctx, (void **)b, nb * sizeof(double)));
-    RS_TRY(dev_alloc(ctx, (void **)&w.act, nb * sizeof(int)));
+    RS_TRY(dev_alloc(ctx, (void **)&w.act, 2 * nb * sizeof(int)));  // active bands | P columns
     w.hbuf_elems = 8 * k + 64;
     if (cudaMallocHost((void **)&w.hbuf, w.hbuf_elems * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();

@@ -14,6 +14,7 @@
 namespace rsdft {
 
 constexpr int NBK = 32;   // block size of the Cholesky and the triangular solves
+constexpr int MAX_K_COOP = 4096;   // largest subspace for the cooperative tridiagonalisation
 
 __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -161,7 +162,9 @@ __global__ void k_hermitise(const double2 *__restrict__ a, int lda, int kc, doub
 }
 
 // ---- triangular solves with the lower factor L (kc x kc) ----------------------------
-// Forward: solve L X = B in place (B: kc x ncol, ld ldb), one block row at a time.
+// Forward: solve L X = B in place (B: kc x ncol, ld ldb), one block row at a
+// time.  Diagonal block: one warp per right-hand-side column, lane r holds row
+// r; column-oriented substitution (x_c final, then rows below subtract it).
 __global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
                                   double2 *b, int ldb, int ncol) {
     __shared__ double2 Ls[NBK][NBK + 1];
@@ -170,20 +173,23 @@ __global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb
         Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
     }
     __syncthreads();
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncol) return;
-    double2 x[NBK];
-    for (int r = 0; r < nb; ++r) {
-        double2 v = b[(size_t)(rb + r) * ldb + col];
-        for (int c = 0; c < r; ++c) {
-            const double2 p = c_mul(Ls[r][c], x[c]);
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (col >= ncol) return;   // whole warps
+    double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
+    for (int c = 0; c < nb; ++c) {
+        const double inv = 1.0 / Ls[c][c].x;   // real positive diagonal
+        double2 x = make_double2(v.x * inv, v.y * inv);
+        x.x = __shfl_sync(0xffffffffu, x.x, c);
+        x.y = __shfl_sync(0xffffffffu, x.y, c);
+        if (lane == c) v = x;
+        else if (lane > c && lane < nb) {
+            const double2 p = c_mul(Ls[lane][c], x);
             v.x -= p.x;
             v.y -= p.y;
         }
-        const double inv = 1.0 / Ls[r][r].x;  // real positive diagonal
-        x[r] = make_double2(v.x * inv, v.y * inv);
     }
-    for (int r = 0; r < nb; ++r) b[(size_t)(rb + r) * ldb + col] = x[r];
+    if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
 }
 
 // b[i][col] -= sum_{c<nb} L[i][rb+c] b[rb+c][col] for i in [rb+nb, kc)
@@ -214,7 +220,8 @@ __global__ void k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int 
     }
 }
 
-// Backward: solve L^H X = B in place, block rows from the bottom.
+// Backward: solve L^H X = B in place, block rows from the bottom.  Diagonal
+// block: one warp per column, lane r holds row r; (L^H)[r][c] = conj(L[c][r]).
 __global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
                                    double2 *b, int ldb, int ncol) {
     __shared__ double2 Ls[NBK][NBK + 1];
@@ -223,21 +230,23 @@ __global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int r
         Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
     }
     __syncthreads();
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (col >= ncol) return;
-    double2 x[NBK];
-    for (int r = nb - 1; r >= 0; --r) {
-        double2 v = b[(size_t)(rb + r) * ldb + col];
-        for (int c = r + 1; c < nb; ++c) {
-            // (L^H)[r][c] = conj(L[c][r])
-            const double2 p = c_mul(c_conj(Ls[c][r]), x[c]);
+    double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
+    for (int c = nb - 1; c >= 0; --c) {
+        const double inv = 1.0 / Ls[c][c].x;
+        double2 x = make_double2(v.x * inv, v.y * inv);
+        x.x = __shfl_sync(0xffffffffu, x.x, c);
+        x.y = __shfl_sync(0xffffffffu, x.y, c);
+        if (lane == c) v = x;
+        else if (lane < c) {
+            const double2 p = c_mul(c_conj(Ls[c][lane]), x);
             v.x -= p.x;
             v.y -= p.y;
         }
-        const double inv = 1.0 / Ls[r][r].x;
-        x[r] = make_double2(v.x * inv, v.y * inv);
     }
-    for (int r = 0; r < nb; ++r) b[(size_t)(rb + r) * ldb + col] = x[r];
+    if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
 }
 
 // b[i][col] -= sum_{c<nb} conj(L[rb+c][i]) b[rb+c][col] for i in [0, rb)
@@ -272,7 +281,7 @@ static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc
                                int ldb, int ncol, cudaStream_t st) {
     for (int rb = 0; rb < kc; rb += NBK) {
         const int nb = std::min(NBK, kc - rb);
-        k_trsm_lower_diag<<<cdiv(ncol, 64), 64, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        k_trsm_lower_diag<<<cdiv(ncol, 8), 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
         count_launch(ctx);
         const int rest = kc - rb - nb;
         if (rest > 0) {
@@ -291,7 +300,7 @@ static rsdft_status trsm_upperH(rsdft_ctx *ctx, const double2 *L, int ldl, int k
     for (int q = nblk - 1; q >= 0; --q) {
         const int rb = q * NBK;
         const int nb = std::min(NBK, kc - rb);
-        k_trsm_upperH_diag<<<cdiv(ncol, 64), 64, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        k_trsm_upperH_diag<<<cdiv(ncol, 8), 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
         count_launch(ctx);
         if (rb > 0) {
             dim3 g(cdiv(ncol, 32), cdiv(rb, 32));
@@ -401,6 +410,173 @@ __global__ void k_house_rank2(double2 *a, int k, int ld, int i, const double2 *_
     double2 &x = a[(size_t)(i + 1 + r) * ld + (i + 1 + c)];
     x.x -= p.x + q.x;
     x.y -= p.y + q.y;
+}
+
+// ---- cooperative tridiagonalisation ------------------------------------------------
+// All Householder steps in one cooperative launch.  Per step i (L = k-i-1):
+//   matvec  w = tau A22 v              (rows over all warps)      -> grid barrier
+//   rank-2  A22 -= v w'^H + w' v^H, w' = w - 1/2 tau (w^H v) v   (entries over all
+//           blocks; block 0 alone updates the next pivot column and then forms
+//           the next reflector)                                    -> grid barrier
+// Data written by other blocks inside the launch is read with ld.global.cg
+// (L2, not the incoherent L1).  Every barrier wait is bounded: on timeout the
+// block sets the error flag and returns, and the others see the flag and return.
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ double2 ldcg2(const double2 *p) { return __ldcg(p); }
+
+__device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, int *s_ok) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vgen = &g->gen;
+        volatile int *verr = &g->err;
+        const unsigned int gen0 = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&g->count, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&g->count, 0u);
+            __threadfence();
+            atomicAdd(&g->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == gen0) {
+                if (*verr) { ok = 0; break; }
+                if (clock64() - t0 > limit) { atomicExch(&g->err, 1); ok = 0; break; }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Reflector of step i from column i of a (block-wide; LAPACK zlarfg convention).
+__device__ void house_reflector_dev(double2 *a, int k, int ld, int i, double2 *vh, int ldv,
+                                    double2 *tau, double *d, double *e, double *sh) {
+    const int L = k - i - 1;
+    const double2 alpha = ldcg2(a + (size_t)(i + 1) * ld + i);
+    double s = 0.0;
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) {
+        const double2 x = ldcg2(a + (size_t)(i + 1 + r) * ld + i);
+        s += x.x * x.x + x.y * x.y;
+    }
+    const double xnorm2 = block_sum(s, sh);
+    double2 t;
+    double beta;
+    double2 scal = make_double2(0.0, 0.0);
+    if (xnorm2 == 0.0 && alpha.y == 0.0) {
+        t = make_double2(0.0, 0.0);
+        beta = alpha.x;
+    } else {
+        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
+        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double dd = den.x * den.x + den.y * den.y;
+        scal = make_double2(den.x / dd, -den.y / dd);
+    }
+    double2 *v = vh + (size_t)i * ldv + (i + 1);
+    for (int r = threadIdx.x; r < L; r += blockDim.x)
+        v[r] = r == 0 ? make_double2(1.0, 0.0) : c_mul(ldcg2(a + (size_t)(i + 1 + r) * ld + i), scal);
+    if (threadIdx.x == 0) {
+        tau[i] = t;
+        e[i] = beta;
+        d[i] = ldcg2(a + (size_t)i * ld + i).x;
+    }
+    __threadfence();
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, double *d, double *e,
+               double2 *w, GridSync *gs, long long limit) {
+    __shared__ double sh[33];
+    __shared__ int s_ok;
+    extern __shared__ double2 s_vw[];      // v then w of the current step, 2k entries
+    double2 *sv = s_vw, *sw = s_vw + k;
+    const unsigned int nb = gridDim.x;
+    if (blockIdx.x == 0 && k >= 2) house_reflector_dev(a, k, ld, 0, vh, ldv, tau, d, e, sh);
+    if (!grid_sync(gs, nb, limit, &s_ok)) return;
+    const int warps = (int)(nb * (blockDim.x >> 5));
+    const int gwarp = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < k - 1; ++i) {
+        const int L = k - i - 1;
+        const double2 ti = ldcg2(tau + i);
+        const double2 *v = vh + (size_t)i * ldv + (i + 1);
+        for (int r = threadIdx.x; r < L; r += blockDim.x) sv[r] = ldcg2(v + r);
+        __syncthreads();
+        // matvec w = tau A22 v, one warp per row
+        for (int r = gwarp; r < L; r += warps) {
+            const double2 *row = a + (size_t)(i + 1 + r) * ld + (i + 1);
+            double sx = 0.0, sy = 0.0;
+#pragma unroll 4
+            for (int c = lane; c < L; c += 32) {
+                const double2 p = c_mul(ldcg2(row + c), sv[c]);
+                sx += p.x;
+                sy += p.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_down_sync(0xffffffffu, sx, o);
+                sy += __shfl_down_sync(0xffffffffu, sy, o);
+            }
+            if (lane == 0) w[r] = c_mul(ti, make_double2(sx, sy));
+        }
+        if (!grid_sync(gs, nb, limit, &s_ok)) return;
+        // alpha = -1/2 tau (w^H v); w' = w + alpha v kept in shared memory
+        double ax = 0.0, ay = 0.0;
+        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+            const double2 wr = ldcg2(w + r);
+            sw[r] = wr;
+            const double2 p = c_mul(c_conj(wr), sv[r]);
+            ax += p.x;
+            ay += p.y;
+        }
+        ax = block_sum(ax, sh);
+        ay = block_sum(ay, sh);
+        const double2 tw = c_mul(ti, make_double2(ax, ay));
+        const double2 alpha = make_double2(-0.5 * tw.x, -0.5 * tw.y);
+        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+            const double2 p = c_mul(alpha, sv[r]);
+            sw[r].x += p.x;
+            sw[r].y += p.y;
+        }
+        __syncthreads();
+        // rank-2 update; column 0 of A22 belongs to block 0
+        if (blockIdx.x == 0) {
+            for (int r = threadIdx.x; r < L; r += blockDim.x) {
+                const double2 p = c_mulc(sv[r], sw[0]), q = c_mulc(sw[r], sv[0]);
+                double2 *x = a + (size_t)(i + 1 + r) * ld + (i + 1);
+                const double2 xv = ldcg2(x);
+                *x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
+            }
+        }
+        const long long tot = (long long)L * L;
+        for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+             idx += (long long)nb * blockDim.x) {
+            const int r = (int)(idx / L), c = (int)(idx % L);
+            if (c == 0) continue;
+            const double2 p = c_mulc(sv[r], sw[c]), q = c_mulc(sw[r], sv[c]);
+            double2 *x = a + (size_t)(i + 1 + r) * ld + (i + 1 + c);
+            const double2 xv = ldcg2(x);
+            *x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
+        }
+        if (blockIdx.x == 0) {
+            __threadfence();
+            __syncthreads();
+            if (i + 1 < k - 1) house_reflector_dev(a, k, ld, i + 1, vh, ldv, tau, d, e, sh);
+            else if (threadIdx.x == 0) d[k - 1] = ldcg2(a + (size_t)(k - 1) * ld + (k - 1)).x;
+        }
+        if (!grid_sync(gs, nb, limit, &s_ok)) return;
+    }
+    if (k == 1 && blockIdx.x == 0 && threadIdx.x == 0) d[0] = a[0].x;
 }
 
 __global__ void k_house_last(const double2 *a, int k, int ld, double *d) {
@@ -631,7 +807,43 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         return RSDFT_OK;
     }
     const int ld = k;
-    for (int i = 0; i < k - 1; ++i) {
+    bool coop_done = false;
+    {
+        // one cooperative launch for all Householder steps
+        static int occ = -1;
+        if (occ < 0) {
+            int attr = 0;
+            cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
+            // the opt-in shared memory size first: the occupancy query below
+            // asks for more than the default 48 KB
+            if (attr == 0 ||
+                cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * MAX_K_COOP * sizeof(double2)) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_coop, 256,
+                                                              2 * MAX_K_COOP * sizeof(double2)) != cudaSuccess)
+                occ = 0;
+            cudaGetLastError();
+        }
+        if (occ > 0 && k <= MAX_K_COOP) {
+            int nb = std::max(1, std::min(ctx->num_sms * std::min(occ, 1), cdiv((long long)k * k, 1024)));
+            GridSync *gs = reinterpret_cast<GridSync *>(w.gsync);
+            RS_CUDA(ctx, cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+            long long limit = 4000000000LL;   // ~2 s of SM clock per barrier wait
+            double2 *vh = w.Vh, *tau = w.tau, *wv = w.wv;
+            double *dd = w.d, *ee = w.e;
+            int kk = k, ldd = ld, ldv = k;
+            void *args[] = {&a, &kk, &ldd, &vh, &ldv, &tau, &dd, &ee, &wv, &gs, &limit};
+            cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_tridiag_coop, dim3(nb), dim3(256),
+                                                        args, 2 * (size_t)k * sizeof(double2), st);
+            if (e == cudaSuccess) {
+                count_launch(ctx);
+                coop_done = true;
+            } else {
+                cudaGetLastError();   // fall back to one launch per phase
+            }
+        }
+    }
+    for (int i = 0; i < k - 1 && !coop_done; ++i) {
         const int L = k - i - 1;
         k_house_reflector<<<1, 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.d, w.e);
         count_launch(ctx);
@@ -643,8 +855,10 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         k_house_rank2<<<g, 128, 0, st>>>(a, k, ld, i, w.Vh, k, w.wv);
         count_launch(ctx);
     }
-    k_house_last<<<1, 1, 0, st>>>(a, k, ld, w.d);
-    count_launch(ctx);
+    if (!coop_done) {
+        k_house_last<<<1, 1, 0, st>>>(a, k, ld, w.d);
+        count_launch(ctx);
+    }
     RS_LAUNCHED(ctx, "householder");
     k_tri_prep<<<1, 1, 0, st>>>(w.d, w.e, k, w.dscr);
     count_launch(ctx);
@@ -657,6 +871,15 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
     count_launch(ctx);
     RS_LAUNCHED(ctx, "tridiagonal eigensolve");
+    if (coop_done) {
+        // a barrier wait of the cooperative kernel that gave up leaves err set
+        int *slot = reinterpret_cast<int *>(w.hbuf + w.hbuf_elems - 16);
+        RS_CUDA(ctx, cudaMemcpyAsync(slot, &reinterpret_cast<GridSync *>(w.gsync)->err, sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+        RS_CUDA(ctx, cudaStreamSynchronize(st));
+        if (*slot != 0)
+            return fail(ctx, RSDFT_E_TIMEOUT, "tridiagonalisation: a grid barrier wait timed out");
+    }
     return RSDFT_OK;
 }
 

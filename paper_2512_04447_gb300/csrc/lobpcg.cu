@@ -8,15 +8,30 @@
 //   Ritz rotation P <- [W P] C_WP, X <- X C_X + P (and HX, HP alike).
 // The host reads back one small vector per iteration (residual norms) plus
 // the kept-column count of the Cholesky.
-#include <cmath>
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "rsdft_internal.h"
 
 namespace rsdft {
 
 constexpr int RTHREADS = 256;
-constexpr double PIVOT_TOL_FP32 = 1e-5;
+// FP32 data path: Gram entries carry ~1e-7 relative error, and the generalised
+// eigenproblem divides the G_H error by the smallest G_S eigenvalue it keeps;
+// a 1e-3 pivot floor bounds that amplification, and bands at the FP32 residual
+// floor are soft-locked.
+constexpr double PIVOT_TOL_FP32 = 1e-3;
+constexpr double LOCK_TOL_FP32 = 1e-6;
+// HP is carried by the rotation, not recomputed: its FP32 rounding is of the
+// order eps32 |HW| |C|, so after normalising a direction p of norm |p| the
+// relative error of H p grows like eps32 / |p|.  Near convergence |p| falls to
+// the residual level and the magnified error produces spurious low Ritz
+// values; P columns with |p| <= 1e-4 therefore leave the basis in the FP32
+// phase (the FP64 phase keeps every P column).  On the 24^3 diamond cell an
+// FP32 run diverged with a 3e-6 threshold and stayed at 5e-8 Ha with 1e-5; 1e-4
+// keeps a factor 10 of margin while leaving unconverged bands their P.
+constexpr double P_DROP_FP32 = 1e-4;
 
 __device__ __forceinline__ double block_sum2(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -242,6 +257,18 @@ struct PhaseEvents {
     }
 };
 
+// G_S = <Y|Y> and G_H = <Y|HY> (Hermitian, ld k): CUDA-core kernels, or for FP32
+// blocks with tc set, one tensor-core launch for both.
+template <typename V>
+static rsdft_status gram_pair(rsdft_ctx *ctx, const RowBlocksT<V> &Y, const RowBlocksT<V> &HY,
+                              double2 *gs, double2 *gh, int k, bool tc, cudaStream_t st) {
+    if constexpr (std::is_same<V, float2>::value) {
+        if (tc) return gram_tc_sh(ctx, Y, HY, gs, gh, k, st);
+    }
+    RS_TRY(Ops<V>::gram(ctx, Y, Y, gs, k, true, ctx->dV, st));
+    return Ops<V>::gram(ctx, Y, HY, gh, k, true, ctx->dV, st);
+}
+
 struct RunState {
     int iterations = 0;
     int dropped = 0;
@@ -266,19 +293,21 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
     V *Pn = (V *)w.Pn, *HPn = (V *)w.HPn, *T1 = (V *)w.T1;
     V *proj = (V *)w.proj;
     int *hact = reinterpret_cast<int *>(w.hbuf + m);
-    // Gram matrices formed from FP32 orbitals carry relative errors ~1e-7, so
-    // a pivot below 1e-5 of the largest diagonal is noise there: the FP32 data
-    // path drops such columns (the FP64 path keeps the caller's floor).
-    const double pivot_tol = sizeof(V) == sizeof(float2) ? std::max(o.pivot_tol, PIVOT_TOL_FP32)
-                                                         : o.pivot_tol;
+    double *hpn = w.hbuf + 2 * m;                         // |P_b| (FP32 phase)
+    int *hactp = reinterpret_cast<int *>(w.hbuf + 3 * m);  // P columns kept
+    int *actp = w.act + m;
+    const bool fp32 = sizeof(V) == sizeof(float2);
+    const bool tc = fp32 && o.tensor_cores != 0;
+    const double pivot_tol = fp32 ? std::max(o.pivot_tol, PIVOT_TOL_FP32) : o.pivot_tol;
+    const double lock_tol = fp32 ? std::max(o.lock_tol, LOCK_TOL_FP32) : o.lock_tol;
+    const double p_drop = fp32 ? P_DROP_FP32 : 0.0;
     if ((const void *)x_in != (const void *)X)
         RS_CUDA(ctx, cudaMemcpyAsync(X, x_in, (size_t)m * n * sizeof(V), cudaMemcpyDeviceToDevice, st));
     RS_TRY(Ops<V>::apply_h(ctx, X, HX, m, st));
     {
         Blocks Y{{X, nullptr, nullptr}, {m, 0, 0}};
         Blocks HY{{HX, nullptr, nullptr}, {m, 0, 0}};
-        RS_TRY(Ops<V>::gram(ctx, Y, Y, w.GS, m, true, dV, st));
-        RS_TRY(Ops<V>::gram(ctx, Y, HY, w.GH, m, true, dV, st));
+        RS_TRY(gram_pair(ctx, Y, HY, w.GS, w.GH, m, tc, st));
         int nd = 0;
         RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, pivot_tol, w.theta, w.Cfull, &nd, st));
         RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
@@ -297,6 +326,12 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         count_launch(ctx);
         RS_LAUNCHED(ctx, "k_resid");
         RS_CUDA(ctx, cudaMemcpyAsync(hres, w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (haveP && p_drop > 0.0) {
+            k_rownorm<V><<<m, RTHREADS, 0, st>>>(P, n, dV, w.nrm);
+            count_launch(ctx);
+            RS_LAUNCHED(ctx, "k_rownorm P");
+            RS_CUDA(ctx, cudaMemcpyAsync(hpn, w.nrm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
         RS_CUDA(ctx, cudaStreamSynchronize(st));
         pe.collect(stats);
         double rmax = 0.0;
@@ -315,9 +350,16 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         prev = rmax;
         int na = 0;
         for (int b = 0; b < m; ++b)
-            if (hres[b] > o.lock_tol) hact[na++] = b;
+            if (hres[b] > lock_tol) hact[na++] = b;
         if (na == 0) break;
+        int np_ = 0;
+        if (haveP) {
+            for (int j = 0; j < na; ++j)
+                if (p_drop <= 0.0 || hpn[hact[j]] > p_drop) hactp[np_++] = hact[j];
+        }
         RS_CUDA(ctx, cudaMemcpyAsync(w.act, hact, na * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (np_ > 0)
+            RS_CUDA(ctx, cudaMemcpyAsync(actp, hactp, np_ * sizeof(int), cudaMemcpyHostToDevice, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[0], st));
         // ---- preconditioned residuals W (compact over the active bands)
         const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
@@ -336,7 +378,12 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         {
             Blocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
             Blocks YW{{W, nullptr, nullptr}, {na, 0, 0}};
-            RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
+            if constexpr (std::is_same<V, float2>::value) {
+                if (tc) RS_TRY(gram_tc(ctx, YX, YW, w.C, na, st));
+                else RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
+            } else {
+                RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
+            }
             RS_TRY(Ops<V>::rotate(ctx, YX, w.C, na, na, W, -1, W, nullptr, st));
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[1], st));
@@ -346,21 +393,19 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         k_scale_rows<V><<<rowgrid, 256, 0, st>>>(W, HW, n, w.nrm);
         count_launch(ctx, 2);
         RS_LAUNCHED(ctx, "normalise W");
-        int np_ = 0;
-        if (haveP) {
-            k_gather_rows<V><<<rowgrid, 256, 0, st>>>(P, HP, w.act, n, Pn, HPn);
-            k_rownorm<V><<<na, RTHREADS, 0, st>>>(Pn, n, dV, w.nrm);
-            k_scale_rows<V><<<rowgrid, 256, 0, st>>>(Pn, HPn, n, w.nrm);
+        if (np_ > 0) {
+            const dim3 pgrid(rowgrid.x, np_);
+            k_gather_rows<V><<<pgrid, 256, 0, st>>>(P, HP, actp, n, Pn, HPn);
+            k_rownorm<V><<<np_, RTHREADS, 0, st>>>(Pn, n, dV, w.nrm);
+            k_scale_rows<V><<<pgrid, 256, 0, st>>>(Pn, HPn, n, w.nrm);
             count_launch(ctx, 3);
             RS_LAUNCHED(ctx, "normalise P");
-            np_ = na;
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[3], st));
         const int k = m + na + np_;
         Blocks Y{{X, W, Pn}, {m, na, np_}};
         Blocks HY{{HX, HW, HPn}, {m, na, np_}};
-        RS_TRY(Ops<V>::gram(ctx, Y, Y, w.GS, k, true, dV, st));
-        RS_TRY(Ops<V>::gram(ctx, Y, HY, w.GH, k, true, dV, st));
+        RS_TRY(gram_pair(ctx, Y, HY, w.GS, w.GH, k, tc, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
         int nd = 0;
         RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
@@ -455,6 +500,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->lock_tol = 1e-10;
     o->pivot_tol = 1e-8;
     o->switch_tol = 1e-4;
+    o->tensor_cores = 0;
 }
 
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,

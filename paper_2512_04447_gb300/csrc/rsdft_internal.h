@@ -68,9 +68,14 @@ struct Workspace {
     double *d = nullptr, *e = nullptr, *lam = nullptr, *zt = nullptr, *dscr = nullptr;
     double *fac = nullptr;   // inverse-iteration factors [k][5][k]
     int *drop = nullptr, *keep = nullptr, *ikeep = nullptr;
+    unsigned int *gsync = nullptr;  // grid-barrier state of the cooperative kernels
+    // tensor-core Gram: BF16 hi/lo operands, FP32 split partials, error flag
+    void *tcbuf = nullptr;  size_t tc_bytes = 0;
+    float *tcpart = nullptr;  size_t tcpart_elems = 0;
+    int *tcerr = nullptr;
     // per-band vectors [cap_band]
     double *theta = nullptr, *res = nullptr, *vexp = nullptr, *tkin = nullptr, *nrm = nullptr;
-    int *act = nullptr;
+    int *act = nullptr;      // [active bands (m) | P columns kept (m)]
     double *hbuf = nullptr;  // pinned host scratch
     size_t hbuf_elems = 0;
 };
@@ -214,6 +219,11 @@ rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocks
                     double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st);
 rsdft_status rotate32(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const double2 *c, int ldc, int m,
                       const float2 *base, int sign, float2 *out0, float2 *out1, cudaStream_t st);
+// Tensor-core (split-BF16, tcgen05) Grams of FP32 blocks (gram_tc.cu).
+rsdft_status gram_tc_sh(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const RowBlocksT<float2> &HY,
+                        double2 *gs, double2 *gh, int ld, cudaStream_t st);
+rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
+                     double2 *g, int ld, cudaStream_t st);
 
 // ---- dense core (dense.cu) ----------------------------------------------------
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,

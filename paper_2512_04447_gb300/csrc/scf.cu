@@ -346,6 +346,7 @@ void rsdft_scf_default_opts(rsdft_scf_opts *o) {
     o->tol = 1e-6;
     o->precond = RSDFT_PRECOND_TPA;
     o->precision = RSDFT_FP64;
+    o->tensor_cores = 0;
 }
 
 static rsdft_status check_scf_opts(rsdft_ctx *ctx, const rsdft_scf_opts *o, int nband) {
@@ -401,6 +402,7 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     lo.precond = opts->precond;
     lo.nconv = opts->kT > 0.0 ? nband : (int)std::min<double>(nband, std::ceil(opts->n_electrons / 2.0));
     lo.precision = opts->precision;
+    lo.tensor_cores = opts->tensor_cores;
     if (s.step == 0) { lo.maxit = opts->first_maxit; lo.tol = opts->tol; }
     else { lo.maxit = opts->k_lobpcg; lo.tol = 0.0; lo.switch_tol = 0.0; }
     rsdft_lobpcg_stats ls{};

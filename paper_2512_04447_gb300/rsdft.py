@@ -49,7 +49,7 @@ class Projectors(C.Structure):
 class LobpcgOpts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("tol", C.c_double), ("nconv", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double),
-                ("switch_tol", C.c_double)]
+                ("switch_tol", C.c_double), ("tensor_cores", C.c_int)]
 
 
 class LobpcgStats(C.Structure):
@@ -65,7 +65,8 @@ class LobpcgStats(C.Structure):
 class ScfOpts(C.Structure):
     _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("beta", C.c_double),
                 ("depth", C.c_int), ("k_lobpcg", C.c_int), ("first_maxit", C.c_int),
-                ("tol", C.c_double), ("precond", C.c_int), ("precision", C.c_int)]
+                ("tol", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
+                ("tensor_cores", C.c_int)]
 
 
 class ScfOut(C.Structure):
@@ -93,6 +94,7 @@ _PROTOS = {
     "rsdft_precondition_tpa": (ip, [vp, vp, vp, vp, ip, vp]),
     "rsdft_gram": (ip, [vp, vp, ip, vp, ip, vp, vp]),
     "rsdft_gram_static": (ip, [vp, ip, vp, ip, C.c_longlong, dp, vp, vp]),
+    "rsdft_gram_bf16x3": (ip, [vp, vp, ip, vp, ip, vp, vp]),
     "rsdft_rotate": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_rayleigh_ritz": (ip, [vp, vp, vp, ip, ip, dp, vp, vp, vp, vp]),
     "rsdft_eigh": (ip, [vp, vp, ip, ip, vp, vp, vp]),
@@ -111,8 +113,8 @@ _PROTOS = {
     "rsdft_launch_count": (C.c_longlong, [vp]),
 }
 
-K_GRAM, K_ROTATE, K_FFT_XY_FWD, K_FFT_Z, K_FFT_XY_INV, K_PROJECT, K_DENSE = range(7)
-KERNEL_NAMES = ["gram", "rotate", "fft_xy_fwd", "fft_z", "fft_xy_inv", "project", "dense"]
+K_GRAM, K_ROTATE, K_FFT_XY_FWD, K_FFT_Z, K_FFT_XY_INV, K_PROJECT, K_DENSE, K_GRAM_TC = range(8)
+KERNEL_NAMES = ["gram", "rotate", "fft_xy_fwd", "fft_z", "fft_xy_inv", "project", "dense", "gram_tc"]
 
 
 def lib() -> C.CDLL:
@@ -265,6 +267,10 @@ class Context:
     def gram(self, a, b, g):
         self._check(lib().rsdft_gram(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(g),
                                      _stream()))
+
+    def gram_bf16x3(self, a, b, g):
+        self._check(lib().rsdft_gram_bf16x3(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0],
+                                            _ptr(g), _stream()))
 
     def rotate(self, y, c, out, base=None, sign=1):
         self._check(lib().rsdft_rotate(self._h, _ptr(y), y.shape[0], _ptr(c), c.shape[1], _ptr(base),

@@ -1,0 +1,70 @@
+"""Tensor-core Gram matrix of the mixed form (split-BF16 x3 on tcgen05, FP32
+accumulation in TMEM, FP64 sums of the K-split partials) against the FP64
+inner products of the same FP32 inputs.
+
+Error model: x = hi + lo with hi = bf16(x), lo = bf16(x - hi); lo keeps 8 of
+the 16 bits left after hi, so each product carries a relative error of about
+2^-16 = 1.5e-5 and the dropped lo*lo' term is ~2^-32.  For the random blocks
+here the entry errors stay below 5e-5 of max |G|."""
+import numpy as np
+import pytest
+
+from oracle.hamiltonian import inner
+from tests.gpu_common import R, dev, host, need_gpu, rel_err, torch
+from workloads import draw_x0
+
+pytestmark = pytest.mark.gpu
+
+BF16X3_TOL = 5e-5
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("N,na,nb", [((20, 18, 15), 1, 1), ((20, 18, 15), 67, 130),
+                                     ((24, 24, 24), 144, 48), ((16, 16, 16), 200, 200)])
+def test_gram_bf16x3_matches_fp64(N, na, nb):
+    ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
+    a = draw_x0(1, na, ctx.n).astype(np.complex64)
+    b = draw_x0(2, nb, ctx.n).astype(np.complex64)
+    g = torch.full((na, nb), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+    ctx.gram_bf16x3(dev(a), dev(b), g)
+    ref = inner(a.astype(np.complex128), b.astype(np.complex128), ctx.dV)
+    err = rel_err(host(g), ref)
+    print(f"split-BF16 Gram {na}x{nb} on {ctx.n} points: max error / max |G| = {err:.2e}")
+    assert err < BF16X3_TOL
+
+
+def test_gram_bf16x3_two_calls_in_a_row_and_hermitian_block():
+    N = (24, 24, 24)
+    ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
+    y = draw_x0(3, 96, ctx.n).astype(np.complex64)
+    ref = inner(y.astype(np.complex128), y.astype(np.complex128), ctx.dV)
+    for _ in range(2):
+        g = torch.empty((96, 96), dtype=torch.complex128, device="cuda")
+        ctx.gram_bf16x3(dev(y), dev(y), g)
+        G = host(g)
+        assert rel_err(G, ref) < BF16X3_TOL
+        assert np.max(np.abs(G - G.conj().T)) < BF16X3_TOL * np.max(np.abs(ref))
+
+
+def test_mixed_lobpcg_with_tensor_core_grams_meets_fp64_bars():
+    """Mixed form with the Gram matrices on the tensor cores: after the FP64
+    refinement the eigenvalues meet the FP64 bar against the oracle."""
+    from oracle.lobpcg import lobpcg as oracle_lobpcg
+    from tests.gpu_common import pair, subspace_distance
+    from workloads import diamond8_24
+    wl = diamond8_24()
+    ctx, ham, _ = pair(wl)
+    x0 = wl.x0(24)
+    x = dev(x0)
+    eig, res, stats, st = ctx.lobpcg(x, ctx.lobpcg_opts(maxit=200, tol=1e-9, precision=R.MIXED,
+                                                        tensor_cores=1))
+    o = oracle_lobpcg(ham, x0, maxit=200, tol=1e-9)
+    print(f"tensor-core mixed LOBPCG: {stats.iterations_mixed} FP32 + "
+          f"{stats.iterations - stats.iterations_mixed} FP64 iterations")
+    assert stats.converged and stats.iterations_mixed > 0
+    assert np.max(np.abs(eig - o.eig)) < 1e-9
+    assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
