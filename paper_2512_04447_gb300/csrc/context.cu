@@ -270,7 +270,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
         RS_TRY(dev_alloc(ctx, (void **)b, k * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.zt, k * k * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.dscr, (8 * k + 64) * sizeof(double)));
-    RS_TRY(dev_alloc(ctx, (void **)&w.fac, 5 * k * k * sizeof(double)));
+    RS_TRY(dev_alloc(ctx, (void **)&w.fac, 6 * k * k * sizeof(double)));   // inverse-iteration factors
     RS_TRY(dev_alloc(ctx, (void **)&w.gsync, 64));
     for (int **b : {&w.drop, &w.keep, &w.ikeep})
         RS_TRY(dev_alloc(ctx, (void **)b, (k + 1) * sizeof(int)));

@@ -55,44 +55,81 @@ __global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double t
     }
 }
 
-// Factor columns kb..kb+nb-1 (rows kb..k-1), in place in the lower triangle.
-__global__ void k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp,
-                             int *drop) {
+// Factor columns kb..kb+nb-1 (rows kb..k-1, nb <= 32), in place in the lower
+// triangle.  Every CTA factors the nb x nb diagonal block in shared memory
+// (column c is dropped when its Schur pivot is <= the floor: l_cc = 1 and
+// L[c+1:, c] = 0); CTA 0 writes it back with the drop flags.  Then each warp
+// solves one row i below the block, l_i = a_i L11^-H, by forward substitution
+// with lane c holding column c: the rows spread over the CTAs (one FP64 chain
+// of nb steps per row) instead of one CTA walking the whole panel.
+__global__ void __launch_bounds__(256)
+k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop) {
+    __shared__ double2 sD[NBK][NBK + 1];
+    __shared__ double s_l[NBK];
+    __shared__ int s_drop[NBK];
     const double floor_ = floorp[0];
-    __shared__ double s_l;
-    __shared__ int s_drop;
-    for (int c = kb; c < kb + nb; ++c) {
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        sD[r][c] = c <= r ? a[(size_t)(kb + r) * ld + kb + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
         if (threadIdx.x == 0) {
-            const double d = a[(size_t)c * ld + c].x;
-            s_drop = !(d > floor_);
-            s_l = s_drop ? 1.0 : sqrt(d);
-            drop[c] = s_drop;
-            a[(size_t)c * ld + c] = make_double2(s_l, 0.0);
+            const double d = sD[c][c].x;
+            const int dr = !(d > floor_);
+            s_drop[c] = dr;
+            s_l[c] = dr ? 1.0 : sqrt(d);
+            sD[c][c] = make_double2(s_l[c], 0.0);
         }
         __syncthreads();
-        const double inv = 1.0 / s_l;
-        for (int i = c + 1 + threadIdx.x; i < k; i += blockDim.x) {
-            double2 &x = a[(size_t)i * ld + c];
-            x = s_drop ? make_double2(0.0, 0.0) : make_double2(x.x * inv, x.y * inv);
+        const int dr = s_drop[c];
+        const double inv = 1.0 / s_l[c];
+        for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+            const double2 x = sD[i][c];
+            sD[i][c] = dr ? make_double2(0.0, 0.0) : make_double2(x.x * inv, x.y * inv);
         }
         __syncthreads();
-        if (!s_drop) {
-            // remaining columns of the panel: a[i][c2] -= l[i][c] conj(l[c2][c]), i >= c2
-            const int ncol = kb + nb - (c + 1);
-            const int nrow = k - (c + 1);
-            for (int t = threadIdx.x; t < ncol * nrow; t += blockDim.x) {
-                const int cc = c + 1 + t / nrow;
-                const int i = c + 1 + t % nrow;
-                if (i < cc) continue;
-                const double2 li = a[(size_t)i * ld + c];
-                const double2 lc = a[(size_t)cc * ld + c];
-                double2 &x = a[(size_t)i * ld + cc];
-                const double2 p = c_mulc(li, lc);
-                x.x -= p.x;
-                x.y -= p.y;
+        if (!dr) {
+            const int m = nb - (c + 1);
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                const int i = c + 1 + t / m, c2 = c + 1 + t % m;
+                if (c2 > i) continue;
+                const double2 p = c_mulc(sD[i][c], sD[c2][c]);
+                sD[i][c2].x -= p.x;
+                sD[i][c2].y -= p.y;
             }
         }
         __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int r = t / nb, c = t % nb;
+            if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = sD[r][c];
+        }
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
+    }
+    // rows below the diagonal block: warp per row, lane c = column kb + c
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int i = kb + nb + (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); i < k; i += warps) {
+        double2 *row = a + (size_t)i * ld + kb;
+        double2 v = lane < nb ? row[lane] : make_double2(0.0, 0.0);
+        for (int c = 0; c < nb; ++c) {
+            double2 x = make_double2(0.0, 0.0);
+            if (lane == c && !s_drop[c]) {
+                const double inv = 1.0 / s_l[c];
+                x = make_double2(v.x * inv, v.y * inv);
+            }
+            x.x = __shfl_sync(0xffffffffu, x.x, c);
+            x.y = __shfl_sync(0xffffffffu, x.y, c);
+            if (lane == c) v = x;
+            else if (lane > c && lane < nb) {
+                const double2 p = c_mulc(x, sD[lane][c]);
+                v.x -= p.x;
+                v.y -= p.y;
+            }
+        }
+        if (lane < nb) row[lane] = v;
     }
 }
 
@@ -413,12 +450,19 @@ __global__ void k_house_rank2(double2 *a, int k, int ld, int i, const double2 *_
 }
 
 // ---- cooperative tridiagonalisation ------------------------------------------------
-// All Householder steps in one cooperative launch.  Per step i (L = k-i-1):
-//   matvec  w = tau A22 v              (rows over all warps)      -> grid barrier
-//   rank-2  A22 -= v w'^H + w' v^H, w' = w - 1/2 tau (w^H v) v   (entries over all
-//           blocks; block 0 alone updates the next pivot column and then forms
-//           the next reflector)                                    -> grid barrier
-// Data written by other blocks inside the launch is read with ld.global.cg
+// All Householder steps in one cooperative launch with ONE grid barrier per
+// step.  With A^(i) the matrix after i reflectors, v_i the i-th reflector (on
+// rows/columns i+1..k-1, v_i[0] = 1) and w_i = tau_i A^(i)_22 v_i known to all
+// blocks after a barrier, step i is, in every block:
+//   w'_i = w_i - 1/2 tau_i (w_i^H v_i) v_i                      (redundant, O(k))
+//   column i+1 of A^(i+1) = column i+1 of A^(i) - v_i conj(w'_i[0]) - w'_i
+//   and its diagonal      -> reflector v_{i+1}, tau_{i+1}, beta  (redundant, O(k))
+// then, over rows r >= i+2 spread over all blocks (row r stays with one warp
+// for the whole launch), the rank-2 update A -= v_i w'^H_i + w'_i v^H_i on
+// columns >= i+2 fused with the next matvec w_{i+1} = tau_{i+1} A^(i+1) v_{i+1}
+//                                                               -> grid barrier.
+// w alternates between two buffers (w_{i+1} is written while slower blocks may
+// still read w_i).  Values written by other blocks are read with ld.global.cg
 // (L2, not the incoherent L1).  Every barrier wait is bounded: on timeout the
 // block sets the error flag and returns, and the others see the flag and return.
 struct GridSync {
@@ -458,90 +502,113 @@ __device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, in
     return *s_ok != 0;
 }
 
-// Reflector of step i from column i of a (block-wide; LAPACK zlarfg convention).
-__device__ void house_reflector_dev(double2 *a, int k, int ld, int i, double2 *vh, int ldv,
-                                    double2 *tau, double *d, double *e, double *sh) {
-    const int L = k - i - 1;
-    const double2 alpha = ldcg2(a + (size_t)(i + 1) * ld + i);
-    double s = 0.0;
-    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) {
-        const double2 x = ldcg2(a + (size_t)(i + 1 + r) * ld + i);
-        s += x.x * x.x + x.y * x.y;
+// Block-wide sum of one complex value.
+__device__ double2 block_sum_c(double2 v, double2 *sh2) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
-    const double xnorm2 = block_sum(s, sh);
-    double2 t;
-    double beta;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh2[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s.x += sh2[w].x;
+            s.y += sh2[w].y;
+        }
+        sh2[32] = s;
+    }
+    __syncthreads();
+    return sh2[32];
+}
+
+// In place: x[0..L) (x[0] = alpha) -> reflector v (v[0] = 1), with tau and
+// beta (LAPACK zlarfg convention: H^H x = beta e_0, H = I - tau v v^H).
+// Block-wide; every thread returns the same tau and beta.
+__device__ void house_inplace(double2 *x, int L, double2 &tau, double &beta, double *sh) {
+    const double2 alpha = x[0];
+    double s = 0.0;
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += x[r].x * x[r].x + x[r].y * x[r].y;
+    const double xnorm2 = block_sum(s, sh);   // its barriers also order the reads of x[0]
     double2 scal = make_double2(0.0, 0.0);
     if (xnorm2 == 0.0 && alpha.y == 0.0) {
-        t = make_double2(0.0, 0.0);
+        tau = make_double2(0.0, 0.0);
         beta = alpha.x;
     } else {
         beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
-        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
         const double2 den = make_double2(alpha.x - beta, alpha.y);
         const double dd = den.x * den.x + den.y * den.y;
         scal = make_double2(den.x / dd, -den.y / dd);
     }
-    double2 *v = vh + (size_t)i * ldv + (i + 1);
-    for (int r = threadIdx.x; r < L; r += blockDim.x)
-        v[r] = r == 0 ? make_double2(1.0, 0.0) : c_mul(ldcg2(a + (size_t)(i + 1 + r) * ld + i), scal);
-    if (threadIdx.x == 0) {
-        tau[i] = t;
-        e[i] = beta;
-        d[i] = ldcg2(a + (size_t)i * ld + i).x;
-    }
-    __threadfence();
+    for (int r = threadIdx.x; r < L; r += blockDim.x) x[r] = r == 0 ? make_double2(1.0, 0.0) : c_mul(x[r], scal);
     __syncthreads();
 }
 
 __global__ void __launch_bounds__(256)
 k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, double *d, double *e,
-               double2 *w, GridSync *gs, long long limit) {
+               double2 *wbuf, GridSync *gs, long long limit) {
     __shared__ double sh[33];
+    __shared__ double2 sh2[33];
     __shared__ int s_ok;
-    extern __shared__ double2 s_vw[];      // v then w of the current step, 2k entries
-    double2 *sv = s_vw, *sw = s_vw + k;
-    const unsigned int nb = gridDim.x;
-    if (blockIdx.x == 0 && k >= 2) house_reflector_dev(a, k, ld, 0, vh, ldv, tau, d, e, sh);
-    if (!grid_sync(gs, nb, limit, &s_ok)) return;
-    const int warps = (int)(nb * (blockDim.x >> 5));
-    const int gwarp = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    const int lane = threadIdx.x & 31;
-    for (int i = 0; i < k - 1; ++i) {
-        const int L = k - i - 1;
-        const double2 ti = ldcg2(tau + i);
-        const double2 *v = vh + (size_t)i * ldv + (i + 1);
-        for (int r = threadIdx.x; r < L; r += blockDim.x) sv[r] = ldcg2(v + r);
-        __syncthreads();
-        // matvec w = tau A22 v, one warp per row
-        for (int r = gwarp; r < L; r += warps) {
-            const double2 *row = a + (size_t)(i + 1 + r) * ld + (i + 1);
-            double sx = 0.0, sy = 0.0;
-#pragma unroll 4
-            for (int c = lane; c < L; c += 32) {
-                const double2 p = c_mul(ldcg2(row + c), sv[c]);
-                sx += p.x;
-                sy += p.y;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                sx += __shfl_down_sync(0xffffffffu, sx, o);
-                sy += __shfl_down_sync(0xffffffffu, sy, o);
-            }
-            if (lane == 0) w[r] = c_mul(ti, make_double2(sx, sy));
+    extern __shared__ double2 s_vw[];      // v_i, w'_i, v_{i+1}: 3k entries
+    double2 *sv = s_vw, *sw = s_vw + k, *sn = s_vw + 2 * k;
+    const int nb = (int)gridDim.x;
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    if (k == 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) d[0] = a[0].x;
+        return;
+    }
+    // reflector 0 from column 0 (every block), then w_0 = tau_0 A[1:,1:] v_0
+    int L = k - 1;
+    for (int r = threadIdx.x; r < L; r += blockDim.x) sv[r] = ldcg2(a + (size_t)(1 + r) * ld);
+    __syncthreads();
+    double2 ti;
+    double beta;
+    house_inplace(sv, L, ti, beta, sh);
+    if (blockIdx.x == 0) {
+        for (int r = threadIdx.x; r < L; r += blockDim.x) vh[1 + r] = sv[r];
+        if (threadIdx.x == 0) {
+            tau[0] = ti;
+            e[0] = beta;
+            d[0] = ldcg2(a).x;
         }
-        if (!grid_sync(gs, nb, limit, &s_ok)) return;
-        // alpha = -1/2 tau (w^H v); w' = w + alpha v kept in shared memory
-        double ax = 0.0, ay = 0.0;
+    }
+    for (int r = blockIdx.x + nb * wib; r < k; r += nb * nwb) {
+        if (r < 1) continue;
+        const double2 *row = a + (size_t)r * ld + 1;
+        double sx = 0.0, sy = 0.0;
+        for (int c = lane; c < L; c += 32) {
+            const double2 p = c_mul(ldcg2(row + c), sv[c]);
+            sx += p.x;
+            sy += p.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) wbuf[r - 1] = c_mul(ti, make_double2(sx, sy));
+    }
+    if (!grid_sync(gs, nb, limit, &s_ok)) return;
+    for (int i = 0; i < k - 1; ++i) {
+        L = k - i - 1;
+        const double2 *w = wbuf + (i & 1) * k;
+        double2 *wn = wbuf + ((i + 1) & 1) * k;
+        // w' = w + alpha v, alpha = -1/2 tau (w^H v); the raw column i+1 is
+        // fetched in the same sweep
+        double2 acc = make_double2(0.0, 0.0);
         for (int r = threadIdx.x; r < L; r += blockDim.x) {
             const double2 wr = ldcg2(w + r);
             sw[r] = wr;
             const double2 p = c_mul(c_conj(wr), sv[r]);
-            ax += p.x;
-            ay += p.y;
+            acc.x += p.x;
+            acc.y += p.y;
+            if (r >= 1) sn[r - 1] = ldcg2(a + (size_t)(i + 1 + r) * ld + (i + 1));
         }
-        ax = block_sum(ax, sh);
-        ay = block_sum(ay, sh);
-        const double2 tw = c_mul(ti, make_double2(ax, ay));
+        acc = block_sum_c(acc, sh2);
+        const double2 tw = c_mul(ti, acc);
         const double2 alpha = make_double2(-0.5 * tw.x, -0.5 * tw.y);
         for (int r = threadIdx.x; r < L; r += blockDim.x) {
             const double2 p = c_mul(alpha, sv[r]);
@@ -549,34 +616,58 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
             sw[r].y += p.y;
         }
         __syncthreads();
-        // rank-2 update; column 0 of A22 belongs to block 0
+        const double dnext = ldcg2(a + (size_t)(i + 1) * ld + (i + 1)).x - 2.0 * sw[0].x;
+        if (i == k - 2) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) d[k - 1] = dnext;
+            break;
+        }
+        // updated column i+1 below the diagonal -> reflector i+1
+        const int Ln = L - 1;
+        for (int q = threadIdx.x; q < Ln; q += blockDim.x) {
+            const double2 p = c_mulc(sv[q + 1], sw[0]), pw = sw[q + 1];
+            sn[q] = make_double2(sn[q].x - p.x - pw.x, sn[q].y - p.y - pw.y);
+        }
+        __syncthreads();
+        double2 tn;
+        double bn;
+        house_inplace(sn, Ln, tn, bn, sh);
         if (blockIdx.x == 0) {
-            for (int r = threadIdx.x; r < L; r += blockDim.x) {
-                const double2 p = c_mulc(sv[r], sw[0]), q = c_mulc(sw[r], sv[0]);
-                double2 *x = a + (size_t)(i + 1 + r) * ld + (i + 1);
-                const double2 xv = ldcg2(x);
-                *x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
+            for (int q = threadIdx.x; q < Ln; q += blockDim.x) vh[(size_t)(i + 1) * ldv + (i + 2) + q] = sn[q];
+            if (threadIdx.x == 0) {
+                tau[i + 1] = tn;
+                e[i + 1] = bn;
+                d[i + 1] = dnext;
             }
         }
-        const long long tot = (long long)L * L;
-        for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-             idx += (long long)nb * blockDim.x) {
-            const int r = (int)(idx / L), c = (int)(idx % L);
-            if (c == 0) continue;
-            const double2 p = c_mulc(sv[r], sw[c]), q = c_mulc(sw[r], sv[c]);
-            double2 *x = a + (size_t)(i + 1 + r) * ld + (i + 1 + c);
-            const double2 xv = ldcg2(x);
-            *x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
-        }
-        if (blockIdx.x == 0) {
-            __threadfence();
-            __syncthreads();
-            if (i + 1 < k - 1) house_reflector_dev(a, k, ld, i + 1, vh, ldv, tau, d, e, sh);
-            else if (threadIdx.x == 0) d[k - 1] = ldcg2(a + (size_t)(k - 1) * ld + (k - 1)).x;
+        // rows >= i+2: A -= v w'^H + w' v^H on columns >= i+2, fused with
+        // w_{i+1} = tau_{i+1} A^(i+1) v_{i+1}
+        const int o = i + 1;
+        for (int r = blockIdx.x + nb * wib; r < k; r += nb * nwb) {
+            if (r < i + 2) continue;
+            double2 *row = a + (size_t)r * ld;
+            const double2 vr = sv[r - o], wr = sw[r - o];
+            double sx = 0.0, sy = 0.0;
+            for (int c = i + 2 + lane; c < k; c += 32) {
+                const double2 xv = ldcg2(row + c);
+                const double2 p = c_mulc(vr, sw[c - o]), q = c_mulc(wr, sv[c - o]);
+                const double2 x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
+                row[c] = x;
+                const double2 m = c_mul(x, sn[c - i - 2]);
+                sx += m.x;
+                sy += m.y;
+            }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o2);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o2);
+            }
+            if (lane == 0) wn[r - i - 2] = c_mul(tn, make_double2(sx, sy));
         }
         if (!grid_sync(gs, nb, limit, &s_ok)) return;
+        double2 *t = sv;
+        sv = sn;
+        sn = t;
+        ti = tn;
     }
-    if (k == 1 && blockIdx.x == 0 && threadIdx.x == 0) d[0] = a[0].x;
 }
 
 __global__ void k_house_last(const double2 *a, int k, int ld, double *d) {
@@ -662,80 +753,106 @@ __device__ __forceinline__ double hash_uniform(unsigned long long x) {
 // Inverse iteration for eigenvalue j: three solves of (T - lam_j I) y = x with
 // partial pivoting (row interchanges), normalising after each solve; the
 // start vector is a fixed pseudo-random one.  Vector j goes to zt[j][0..k).
-// fac: per-eigenvalue scratch [nkeep][5][k] (U0, U1, U2, multipliers, swaps).
-__global__ void k_inverse_iter(const double *d, const double *e, int k, int nkeep,
-                               const double *lam, const double *scr, double *fac, double *zt) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per eigenvalue (one CTA each, so the eigenvalues spread over the
+// SMs): lane 0 runs the sequential elimination and substitutions, the warp
+// does the element-wise parts.  The factors live in shared memory when 6k
+// doubles fit (smem != 0), else in the per-eigenvalue scratch fac[j][6][k].
+__global__ void __launch_bounds__(32)
+k_inverse_iter(const double *d, const double *e, int k, int nkeep, const double *lam,
+               const double *scr, double *fac, double *zt, int smem) {
+    extern __shared__ double s_fac[];
+    const int j = blockIdx.x;
     if (j >= nkeep) return;
+    const int lane = threadIdx.x;
     const double tiny = DBL_EPSILON * fmax(scr[0], 1e-300);
-    double *D = fac + (size_t)j * 5 * k;
-    double *U1 = D + k, *U2 = U1 + k, *M = U2 + k, *F = M + k;
-    double *x = zt + (size_t)j * k;
+    double *D = smem ? s_fac : fac + (size_t)j * 6 * k;
+    double *U1 = D + k, *U2 = U1 + k, *M = U2 + k, *F = M + k, *x = F + k;
     const double s = lam[j];
-    for (int i = 0; i < k; ++i) {
+    for (int i = lane; i < k; i += 32) {
         D[i] = d[i] - s;
         U1[i] = i < k - 1 ? e[i] : 0.0;
         U2[i] = 0.0;
         M[i] = 0.0;
         F[i] = 0.0;
-    }
-    for (int i = 0; i < k - 1; ++i) {
-        const double sub = e[i];
-        if (fabs(D[i]) >= fabs(sub)) {
-            if (D[i] == 0.0) D[i] = tiny;
-            M[i] = sub / D[i];
-            D[i + 1] -= M[i] * U1[i];
-        } else {
-            // interchange rows i and i+1, then eliminate
-            const double mult = D[i] / sub;
-            const double dk1 = D[i + 1], uk = U1[i], uk1 = U1[i + 1];
-            D[i] = sub;
-            U1[i] = dk1;
-            U2[i] = uk1;
-            D[i + 1] = uk - mult * dk1;
-            U1[i + 1] = -mult * uk1;
-            M[i] = mult;
-            F[i] = 1.0;
-        }
-    }
-    for (int i = 0; i < k; ++i)
-        if (fabs(D[i]) < tiny) D[i] = D[i] < 0.0 ? -tiny : tiny;
-    for (int i = 0; i < k; ++i)
         x[i] = hash_uniform(((unsigned long long)(j + 1) << 32) + (unsigned long long)i);
-    for (int it = 0; it < 3; ++it) {
+    }
+    __syncwarp();
+    if (lane == 0) {
         for (int i = 0; i < k - 1; ++i) {
-            if (F[i] != 0.0) {
-                const double t = x[i];
-                x[i] = x[i + 1];
-                x[i + 1] = t - M[i] * x[i];
+            const double sub = e[i];
+            if (fabs(D[i]) >= fabs(sub)) {
+                if (D[i] == 0.0) D[i] = tiny;
+                M[i] = sub / D[i];
+                D[i + 1] -= M[i] * U1[i];
             } else {
-                x[i + 1] -= M[i] * x[i];
+                // interchange rows i and i+1, then eliminate
+                const double mult = D[i] / sub;
+                const double dk1 = D[i + 1], uk = U1[i], uk1 = U1[i + 1];
+                D[i] = sub;
+                U1[i] = dk1;
+                U2[i] = uk1;
+                D[i + 1] = uk - mult * dk1;
+                U1[i + 1] = -mult * uk1;
+                M[i] = mult;
+                F[i] = 1.0;
             }
         }
-        x[k - 1] /= D[k - 1];
-        if (k >= 2) x[k - 2] = (x[k - 2] - U1[k - 2] * x[k - 1]) / D[k - 2];
-        for (int i = k - 3; i >= 0; --i) x[i] = (x[i] - U1[i] * x[i + 1] - U2[i] * x[i + 2]) / D[i];
-        double nrm = 0.0;
-        for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
-        nrm = 1.0 / sqrt(nrm);
-        for (int i = 0; i < k; ++i) x[i] *= nrm;
     }
+    __syncwarp();
+    // clamp tiny pivots, then keep 1/D for the substitutions
+    for (int i = lane; i < k; i += 32) {
+        double di = D[i];
+        if (fabs(di) < tiny) di = di < 0.0 ? -tiny : tiny;
+        D[i] = 1.0 / di;
+    }
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+        if (lane == 0) {
+            for (int i = 0; i < k - 1; ++i) {
+                if (F[i] != 0.0) {
+                    const double t = x[i];
+                    x[i] = x[i + 1];
+                    x[i + 1] = t - M[i] * x[i];
+                } else {
+                    x[i + 1] -= M[i] * x[i];
+                }
+            }
+            x[k - 1] *= D[k - 1];
+            if (k >= 2) x[k - 2] = (x[k - 2] - U1[k - 2] * x[k - 1]) * D[k - 2];
+            for (int i = k - 3; i >= 0; --i) x[i] = (x[i] - U1[i] * x[i + 1] - U2[i] * x[i + 2]) * D[i];
+        }
+        __syncwarp();
+        double nrm = 0.0;
+        for (int i = lane; i < k; i += 32) nrm += x[i] * x[i];
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = lane; i < k; i += 32) x[i] *= nrm;
+        __syncwarp();
+    }
+    double *out = zt + (size_t)j * k;
+    for (int i = lane; i < k; i += 32) out[i] = x[i];
 }
 
 // Gram-Schmidt (two passes) of each vector against the earlier vectors of its
-// eigenvalue cluster (consecutive eigenvalues closer than 1e-3 ||T||).
+// eigenvalue cluster (a maximal run of consecutive eigenvalues with gaps of at
+// most 1e-3 ||T||), then normalisation.  Clusters are independent: CTA j
+// handles the cluster that starts at eigenvalue j; singletons are left as
+// inverse iteration normalised them.
 __global__ void k_cluster_gs(int k, int nkeep, const double *lam, const double *scr, double *zt) {
     __shared__ double sh[33];
     __shared__ double dots[1024];
     const double ortol = 1e-3 * scr[0];
-    int cstart = 0;
-    for (int j = 0; j < nkeep; ++j) {
-        if (j > 0 && !(lam[j] - lam[j - 1] <= ortol)) cstart = j;
+    const int cstart = blockIdx.x;
+    if (cstart >= nkeep) return;
+    if (cstart > 0 && lam[cstart] - lam[cstart - 1] <= ortol) return;   // not a cluster start
+    int cend = cstart + 1;
+    while (cend < nkeep && lam[cend] - lam[cend - 1] <= ortol) ++cend;
+    if (cend - cstart < 2) return;
+    for (int j = cstart + 1; j < cend; ++j) {
         double *x = zt + (size_t)j * k;
-        for (int pass = 0; pass < 2 && cstart < j; ++pass) {
+        for (int pass = 0; pass < 2; ++pass) {
             for (int i0 = cstart; i0 < j; i0 += 1024) {
                 const int cnt = min(1024, j - i0);
-                // dots by warps
                 const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
                 for (int q = warp; q < cnt; q += nw) {
                     const double *y = zt + (size_t)(i0 + q) * k;
@@ -818,9 +935,9 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
             // asks for more than the default 48 KB
             if (attr == 0 ||
                 cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * MAX_K_COOP * sizeof(double2)) != cudaSuccess ||
+                                     3 * MAX_K_COOP * sizeof(double2)) != cudaSuccess ||
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_coop, 256,
-                                                              2 * MAX_K_COOP * sizeof(double2)) != cudaSuccess)
+                                                              3 * MAX_K_COOP * sizeof(double2)) != cudaSuccess)
                 occ = 0;
             cudaGetLastError();
         }
@@ -834,7 +951,7 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
             int kk = k, ldd = ld, ldv = k;
             void *args[] = {&a, &kk, &ldd, &vh, &ldv, &tau, &dd, &ee, &wv, &gs, &limit};
             cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_tridiag_coop, dim3(nb), dim3(256),
-                                                        args, 2 * (size_t)k * sizeof(double2), st);
+                                                        args, 3 * (size_t)k * sizeof(double2), st);
             if (e == cudaSuccess) {
                 count_launch(ctx);
                 coop_done = true;
@@ -862,11 +979,25 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     RS_LAUNCHED(ctx, "householder");
     k_tri_prep<<<1, 1, 0, st>>>(w.d, w.e, k, w.dscr);
     count_launch(ctx);
-    k_bisect<<<cdiv(nkeep, 4), 128, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+    // one warp per eigenvalue and one CTA per warp: the Sturm counts and the
+    // substitutions are FP64 chains, so the eigenvalues spread over the SMs
+    k_bisect<<<nkeep, 32, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
     count_launch(ctx);
-    k_inverse_iter<<<cdiv(nkeep, 32), 32, 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr, w.fac, w.zt);
+    {
+        const size_t ii_smem = (size_t)6 * k * sizeof(double);
+        static size_t ii_smem_max = 0;
+        if (ii_smem > 48 * 1024 && ii_smem > ii_smem_max && ii_smem <= 200 * 1024) {
+            if (cudaFuncSetAttribute(k_inverse_iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ii_smem) == cudaSuccess)
+                ii_smem_max = ii_smem;
+            cudaGetLastError();
+        }
+        const bool use_smem = ii_smem <= 48 * 1024 || ii_smem <= ii_smem_max;
+        k_inverse_iter<<<nkeep, 32, use_smem ? ii_smem : 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr,
+                                                                   w.fac, w.zt, use_smem ? 1 : 0);
+    }
     count_launch(ctx);
-    k_cluster_gs<<<1, 512, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
+    k_cluster_gs<<<nkeep, 256, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
     count_launch(ctx);
     k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
     count_launch(ctx);
@@ -906,7 +1037,8 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     count_launch(ctx);
     for (int kb = 0; kb < k; kb += NBK) {
         const int nb = std::min(NBK, k - kb);
-        k_chol_panel<<<1, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4, w.drop);
+        k_chol_panel<<<std::max(1, cdiv(k - kb - nb, 8)), 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4,
+                                                                         w.drop);
         count_launch(ctx);
         const int rest = k - kb - nb;
         if (rest > 0) {

@@ -66,7 +66,7 @@ struct Workspace {
     double2 *Lm = nullptr, *Km = nullptr, *Ym = nullptr, *Vh = nullptr, *Zc = nullptr;
     double2 *tau = nullptr, *wv = nullptr;
     double *d = nullptr, *e = nullptr, *lam = nullptr, *zt = nullptr, *dscr = nullptr;
-    double *fac = nullptr;   // inverse-iteration factors [k][5][k]
+    double *fac = nullptr;   // inverse-iteration factors and vector [k][6][k] (shared-memory overflow)
     int *drop = nullptr, *keep = nullptr, *ikeep = nullptr;
     unsigned int *gsync = nullptr;  // grid-barrier state of the cooperative kernels
     // tensor-core Gram: BF16 hi/lo operands, FP32 split partials, error flag
