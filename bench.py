@@ -184,6 +184,22 @@ def kernel_roofline(name, d, precision, sm_mhz, hbm_gbs):
     if s <= 0 or d["launches"] == 0:
         return None
     fp32 = precision != "fp64"
+    if name == "rotate_tc":
+        # split-BF16 x3 rotation: reads the split rows of Y once, writes X and P;
+        # at 144 bands it sits near both ridges, so report the tighter bound
+        s_ = d["ms"] / 1e3
+        tf = d["flops"] / s_ / 1e12
+        gbs = d["bytes"] / s_ / 1e9
+        peak_tf = float(_peaks().get("bf16_tflops", 1955.4))
+        common = {"kernel": name, "avg_launch_ms": s_ / d["launches"] * 1e3,
+                  "algorithmic_flops_per_launch": d["flops"] / d["launches"],
+                  "algorithmic_bytes_per_launch": d["bytes"] / d["launches"]}
+        if tf / peak_tf >= gbs / hbm_gbs:
+            return dict(common, bound="tensor", achieved=tf, peak=peak_tf, unit="TFLOP/s",
+                        frac=tf / peak_tf,
+                        peak_source="MEASURED_PEAKS.json bf16_tflops (cuBLAS BF16 GEMM, burst)")
+        return dict(common, bound="hbm", achieved=gbs, peak=hbm_gbs, unit="GB/s", frac=gbs / hbm_gbs,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs (copy bandwidth, measured)")
     if name == "gram_tc":
         # split-BF16 x3 on tcgen05: three BF16 MMAs per product, against the
         # measured dense BF16 tensor peak
@@ -217,7 +233,7 @@ def time_form(ctx, R, torch, x0, wl, precision, args, barrier, stream):
     prec = R.FP64 if precision == "fp64" else R.MIXED
     opts = ctx.scf_opts(n_electrons=wl.n_electrons, kT=wl.kT, beta=0.3, depth=4, k_lobpcg=3,
                         first_maxit=200, tol=1e-6, precision=prec,
-                        tensor_cores=1 if precision == "mixed_tc" else 0)
+                        tensor_cores=2 if precision == "mixed_tc" else 0)
     x = torch.from_numpy(x0).cuda()
     ctx.scf_init(wl.nband, opts)
     barrier()
@@ -245,6 +261,7 @@ def time_form(ctx, R, torch, x0, wl, precision, args, barrier, stream):
     kern = {name: ctx.profile_read(kid) for kid, name in enumerate(R.KERNEL_NAMES)}
     ctx.profile_enable(False)
     return {"x": x, "opts": opts, "t_first": t_first, "first_iters": out0.lobpcg_iterations,
+            "first_iters_fp32": out0.lobpcg_iterations_mixed,
             "eig0": eig0, "total_ms": total_ms, "launches": launches, "kern": kern, "outs": outs}
 
 
@@ -314,6 +331,7 @@ def run_ours(args, rank, world, local_rank):
         summary[f] = {"s_per_scf_step": job_value(r["total_ms"], args.steps, world),
                       "lobpcg_time_to_1e-6_s": r["t_first"],
                       "first_step_lobpcg_iterations": r["first_iters"],
+                      "first_step_lobpcg_iterations_fp32": r["first_iters_fp32"],
                       "gpu_launches": r["launches"], "kernels": kern,
                       "scf_last": {k: r["outs"][-1][k] for k in ("e_tot", "drho", "step")}}
     if "fp64" in res:
@@ -342,8 +360,9 @@ def run_ours(args, rank, world, local_rank):
                                      "mixed": "mixed: FP32 orbitals for H psi/FFT/Gram/rotation, "
                                               "FP64 norms and dense core; first solve refined in "
                                               "FP64 to 1e-6 Ha",
-                                     "mixed_tc": "mixed as above with the Gram matrices as "
-                                                 "split-BF16 x3 tcgen05 GEMMs (FP32 accumulation)"}[head],
+                                     "mixed_tc": "mixed as above with the Gram matrices and "
+                                                 "the Ritz rotations as split-BF16 x3 tcgen05 "
+                                                 "GEMMs (FP32 accumulation in TMEM)"}[head],
                        "learned_preconditioner": "not built (TPA in both forms)",
                        "l2": "inputs larger than L2 (orbital block 604 MB vs 129 MB L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -376,7 +395,14 @@ def run_profile_case(case):
     ctx = R.Context((10.11,) * 3, N, np.zeros(N[0] * N[1] * N[2]))
     g = torch.Generator(device="cuda").manual_seed(0)
     cdt = torch.complex64 if case.endswith("32") else torch.complex128
-    if case == "gram_tc":
+    if case == "rotate_tc":
+        # split-BF16 tensor-core rotation of a 432-row FP32 block into 144 bands
+        y = torch.randn(432, ctx.n, dtype=torch.complex64, device="cuda", generator=g)
+        c = torch.randn(432, 144, dtype=torch.complex128, device="cuda", generator=g)
+        o0 = torch.empty(144, ctx.n, dtype=torch.complex64, device="cuda")
+        o1 = torch.empty_like(o0)
+        ctx.rotate_bf16x3(y, c, o0, o1)
+    elif case == "gram_tc":
         # split-BF16 tensor-core Gram of a 432-row FP32 block (382 MB)
         y = torch.randn(432, ctx.n, dtype=torch.complex64, device="cuda", generator=g)
         gm = torch.empty(432, 432, dtype=torch.complex128, device="cuda")
@@ -409,7 +435,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed", "mixed_tc"])
     ap.add_argument("--profile-case", default=None,
-                    help="run one small case for ncu (gram, gram_tc, rotate, hpsi, hpsi32) and exit")
+                    help="run one small case for ncu (gram, gram_tc, rotate, rotate_tc, hpsi, hpsi32) and exit")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)

@@ -167,6 +167,19 @@ rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int
 rsdft_status rsdft_gram_bf16x3(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
                                void *g_dev, void *stream);
 
+/* Ritz rotation of a complex64 block on the tensor cores (the mixed form's
+ * rotation, SCF task (2)): with Y = y_dev [k][n] complex64 and C = c_dev [k][m]
+ * complex128 row-major (rows 0..m-1 multiply the X part, m..k-1 the [W P] part),
+ *   out1[b] = sum_{i >= m} C[i][b] Y[i]        (the new P)
+ *   out0[b] = sum_{i <  m} C[i][b] Y[i] + out1[b]   (the new X)
+ * as real GEMMs over the interleaved grid index with Y and C split into bf16
+ * hi + lo and the products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM.
+ * out0_dev, out1_dev: [m][n] complex64, caller-owned, must not alias y_dev.
+ * Shape limits: 1 <= m <= 240 and k > m, else RSDFT_E_INVALID.  Relative
+ * error about 1e-5 of the largest |C[i][b] Y[i](r)| term. */
+rsdft_status rsdft_rotate_bf16x3(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
+                                 void *out0_dev, void *out1_dev, void *stream);
+
 /* Rotation out[b] = sum_i c[i][b] y[i] (+ base[b] when base_dev != NULL;
  * base may alias out).  y_dev: [k][n]; c_dev: [k][m] row-major;
  * out_dev, base_dev: [m][n]; complex128.  sign = +1 adds, -1 subtracts the sum. */
@@ -214,9 +227,11 @@ typedef struct {
                               is <= max(tol, switch_tol) (1e-4) or stagnates (3
                               iterations gaining < 10%), then FP64 to tol; 0 runs
                               FP32 iterations to maxit                            */
-    int tensor_cores;      /* RSDFT_MIXED: 1 forms the Gram matrices of the FP32
-                              phase with split-BF16 tcgen05 GEMMs, 0 with FP32
-                              CUDA cores (default 0)                              */
+    int tensor_cores;      /* RSDFT_MIXED: 0 runs the FP32 phase's Gram matrices
+                              and Ritz rotations on FP32 CUDA cores; 1 forms the
+                              Gram matrices with split-BF16 tcgen05 GEMMs; 2 does
+                              the Ritz rotations that way too (when m <= 240)
+                              (default 0)                                         */
 } rsdft_lobpcg_opts;
 
 typedef struct {
@@ -263,6 +278,7 @@ typedef struct {
     double e_band, e_h, e_xc, e_vxc, mu, entropy;
     double drho;           /* ||rho_out - rho_in|| sqrt(dV)                        */
     int lobpcg_iterations;
+    int lobpcg_iterations_mixed;  /* of which on the FP32 data path (RSDFT_MIXED)  */
     int step;              /* index of the step just done (0-based)                */
 } rsdft_scf_out;
 
@@ -307,7 +323,8 @@ typedef enum {
     RSDFT_K_PROJECT = 5,     /* projector gather <beta|psi>                     */
     RSDFT_K_DENSE = 6,       /* Cholesky, TRSM, eigensolve of the subspace      */
     RSDFT_K_GRAM_TC = 7,     /* tensor-core split-BF16 Gram (tcgen05)           */
-    RSDFT_K_COUNT = 8
+    RSDFT_K_ROTATE_TC = 8,   /* tensor-core split-BF16 Ritz rotation (tcgen05)  */
+    RSDFT_K_COUNT = 9
 } rsdft_kernel_id;
 
 rsdft_status rsdft_profile_enable(rsdft_ctx *ctx, int on);

@@ -65,7 +65,7 @@ __global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double t
 __global__ void __launch_bounds__(256)
 k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop) {
     __shared__ double2 sD[NBK][NBK + 1];
-    __shared__ double s_l[NBK];
+    __shared__ double s_l[NBK], s_il[NBK];   // pivots and their reciprocals
     __shared__ int s_drop[NBK];
     const double floor_ = floorp[0];
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
@@ -79,11 +79,12 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
             const int dr = !(d > floor_);
             s_drop[c] = dr;
             s_l[c] = dr ? 1.0 : sqrt(d);
+            s_il[c] = dr ? 1.0 : 1.0 / s_l[c];
             sD[c][c] = make_double2(s_l[c], 0.0);
         }
         __syncthreads();
         const int dr = s_drop[c];
-        const double inv = 1.0 / s_l[c];
+        const double inv = s_il[c];
         for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) {
             const double2 x = sD[i][c];
             sD[i][c] = dr ? make_double2(0.0, 0.0) : make_double2(x.x * inv, x.y * inv);
@@ -117,7 +118,7 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
         for (int c = 0; c < nb; ++c) {
             double2 x = make_double2(0.0, 0.0);
             if (lane == c && !s_drop[c]) {
-                const double inv = 1.0 / s_l[c];
+                const double inv = s_il[c];
                 x = make_double2(v.x * inv, v.y * inv);
             }
             x.x = __shfl_sync(0xffffffffu, x.x, c);
@@ -205,17 +206,19 @@ __global__ void k_hermitise(const double2 *__restrict__ a, int lda, int kc, doub
 __global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
                                   double2 *b, int ldb, int ncol) {
     __shared__ double2 Ls[NBK][NBK + 1];
+    __shared__ double Linv[NBK];   // reciprocal pivots, formed once per CTA
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
         Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
     }
+    if (threadIdx.x < nb) Linv[threadIdx.x] = 1.0 / L[(size_t)(rb + threadIdx.x) * ldl + rb + threadIdx.x].x;
     __syncthreads();
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (col >= ncol) return;   // whole warps
     double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
     for (int c = 0; c < nb; ++c) {
-        const double inv = 1.0 / Ls[c][c].x;   // real positive diagonal
+        const double inv = Linv[c];   // real positive diagonal
         double2 x = make_double2(v.x * inv, v.y * inv);
         x.x = __shfl_sync(0xffffffffu, x.x, c);
         x.y = __shfl_sync(0xffffffffu, x.y, c);
@@ -229,32 +232,36 @@ __global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb
     if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
 }
 
-// b[i][col] -= sum_{c<nb} L[i][rb+c] b[rb+c][col] for i in [rb+nb, kc)
-__global__ void k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int kc, int rb, int nb,
-                                    double2 *b, int ldb, int ncol) {
-    const int i0 = rb + nb + blockIdx.y * 32, c0 = blockIdx.x * 32;
-    __shared__ double2 Ls[32][NBK + 1], Xs[NBK][33];
-    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+// b[i][col] -= sum_{c<nb} L[i][rb+c] b[rb+c][col] for i in [rb+nb, kc); tiles of
+// TRSM_TR rows x 32 columns, one output per thread (small tiles balance the
+// FP64 work over the SMs).
+constexpr int TRSM_TR = 8;
+__global__ void __launch_bounds__(256)
+k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int kc, int rb, int nb, double2 *b, int ldb,
+                    int ncol) {
+    const int i0 = rb + nb + blockIdx.y * TRSM_TR, c0 = blockIdx.x * 32;
+    __shared__ double2 Ls[TRSM_TR][NBK + 1], Xs[NBK][33];
+    for (int t = threadIdx.x; t < TRSM_TR * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
         Ls[r][c] = (i0 + r < kc) ? L[(size_t)(i0 + r) * ldl + rb + c] : make_double2(0.0, 0.0);
+    }
+    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
         const int xr = t / 32, xc = t % 32;
         Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-        const int r = t / 32, s = t % 32;
-        const int i = i0 + r, col = c0 + s;
-        if (i >= kc || col >= ncol) continue;
-        double sx = 0.0, sy = 0.0;
-        for (int c = 0; c < nb; ++c) {
-            const double2 p = c_mul(Ls[r][c], Xs[c][s]);
-            sx += p.x;
-            sy += p.y;
-        }
-        double2 &x = b[(size_t)i * ldb + col];
-        x.x -= sx;
-        x.y -= sy;
+    const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
+    const int i = i0 + r, col = c0 + s_;
+    if (i >= kc || col >= ncol) return;
+    double sx = 0.0, sy = 0.0;
+    for (int c = 0; c < nb; ++c) {
+        const double2 p = c_mul(Ls[r][c], Xs[c][s_]);
+        sx += p.x;
+        sy += p.y;
     }
+    double2 &x = b[(size_t)i * ldb + col];
+    x.x -= sx;
+    x.y -= sy;
 }
 
 // Backward: solve L^H X = B in place, block rows from the bottom.  Diagonal
@@ -262,17 +269,19 @@ __global__ void k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int 
 __global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
                                    double2 *b, int ldb, int ncol) {
     __shared__ double2 Ls[NBK][NBK + 1];
+    __shared__ double Linv[NBK];   // reciprocal pivots, formed once per CTA
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
         Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
     }
+    if (threadIdx.x < nb) Linv[threadIdx.x] = 1.0 / L[(size_t)(rb + threadIdx.x) * ldl + rb + threadIdx.x].x;
     __syncthreads();
     const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (col >= ncol) return;
     double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
     for (int c = nb - 1; c >= 0; --c) {
-        const double inv = 1.0 / Ls[c][c].x;
+        const double inv = Linv[c];
         double2 x = make_double2(v.x * inv, v.y * inv);
         x.x = __shfl_sync(0xffffffffu, x.x, c);
         x.y = __shfl_sync(0xffffffffu, x.y, c);
@@ -286,32 +295,33 @@ __global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int r
     if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
 }
 
-// b[i][col] -= sum_{c<nb} conj(L[rb+c][i]) b[rb+c][col] for i in [0, rb)
-__global__ void k_trsm_upperH_update(const double2 *__restrict__ L, int ldl, int rb, int nb,
-                                     double2 *b, int ldb, int ncol) {
-    const int i0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    __shared__ double2 Ls[32][NBK + 1], Xs[NBK][33];
-    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+// b[i][col] -= sum_{c<nb} conj(L[rb+c][i]) b[rb+c][col] for i in [0, rb); tiles as above.
+__global__ void __launch_bounds__(256)
+k_trsm_upperH_update(const double2 *__restrict__ L, int ldl, int rb, int nb, double2 *b, int ldb,
+                     int ncol) {
+    const int i0 = blockIdx.y * TRSM_TR, c0 = blockIdx.x * 32;
+    __shared__ double2 Ls[TRSM_TR][NBK + 1], Xs[NBK][33];
+    for (int t = threadIdx.x; t < TRSM_TR * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
         Ls[r][c] = (i0 + r < rb) ? c_conj(L[(size_t)(rb + c) * ldl + i0 + r]) : make_double2(0.0, 0.0);
+    }
+    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
         const int xr = t / 32, xc = t % 32;
         Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-        const int r = t / 32, s = t % 32;
-        const int i = i0 + r, col = c0 + s;
-        if (i >= rb || col >= ncol) continue;
-        double sx = 0.0, sy = 0.0;
-        for (int c = 0; c < nb; ++c) {
-            const double2 p = c_mul(Ls[r][c], Xs[c][s]);
-            sx += p.x;
-            sy += p.y;
-        }
-        double2 &x = b[(size_t)i * ldb + col];
-        x.x -= sx;
-        x.y -= sy;
+    const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
+    const int i = i0 + r, col = c0 + s_;
+    if (i >= rb || col >= ncol) return;
+    double sx = 0.0, sy = 0.0;
+    for (int c = 0; c < nb; ++c) {
+        const double2 p = c_mul(Ls[r][c], Xs[c][s_]);
+        sx += p.x;
+        sy += p.y;
     }
+    double2 &x = b[(size_t)i * ldb + col];
+    x.x -= sx;
+    x.y -= sy;
 }
 
 static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
@@ -322,7 +332,7 @@ static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc
         count_launch(ctx);
         const int rest = kc - rb - nb;
         if (rest > 0) {
-            dim3 g(cdiv(ncol, 32), cdiv(rest, 32));
+            dim3 g(cdiv(ncol, 32), cdiv(rest, TRSM_TR));
             k_trsm_lower_update<<<g, 256, 0, st>>>(L, ldl, kc, rb, nb, b, ldb, ncol);
             count_launch(ctx);
         }
@@ -340,7 +350,7 @@ static rsdft_status trsm_upperH(rsdft_ctx *ctx, const double2 *L, int ldl, int k
         k_trsm_upperH_diag<<<cdiv(ncol, 8), 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
         count_launch(ctx);
         if (rb > 0) {
-            dim3 g(cdiv(ncol, 32), cdiv(rb, 32));
+            dim3 g(cdiv(ncol, 32), cdiv(rb, TRSM_TR));
             k_trsm_upperH_update<<<g, 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
             count_launch(ctx);
         }
@@ -474,26 +484,24 @@ struct GridSync {
 
 __device__ __forceinline__ double2 ldcg2(const double2 *p) { return __ldcg(p); }
 
-__device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, int *s_ok) {
+// Grid barrier on a monotonic arrival counter (zeroed before the launch): the
+// e-th barrier of the launch completes when count reaches nblocks * (e + 1).
+// The wait is bounded by `limit` SM cycles; a block that gives up sets the
+// error flag, and blocks that see the flag stop waiting.
+__device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, int *s_ok, unsigned int &epoch) {
     __threadfence();
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *vgen = &g->gen;
+        volatile unsigned int *vcount = &g->count;
         volatile int *verr = &g->err;
-        const unsigned int gen0 = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&g->count, 1u) + 1u;
-        if (arrived == nblocks) {
-            atomicExch(&g->count, 0u);
-            __threadfence();
-            atomicAdd(&g->gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*vgen == gen0) {
-                if (*verr) { ok = 0; break; }
-                if (clock64() - t0 > limit) { atomicExch(&g->err, 1); ok = 0; break; }
-            }
+        const unsigned int target = nblocks * epoch;
+        atomicAdd(&g->count, 1u);
+        const long long t0 = clock64();
+        while (*vcount < target) {
+            if (*verr) { ok = 0; break; }
+            if (clock64() - t0 > limit) { atomicExch(&g->err, 1); ok = 0; break; }
         }
         __threadfence();
         *s_ok = ok;
@@ -532,17 +540,31 @@ __device__ void house_inplace(double2 *x, int L, double2 &tau, double &beta, dou
     double s = 0.0;
     for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += x[r].x * x[r].x + x[r].y * x[r].y;
     const double xnorm2 = block_sum(s, sh);   // its barriers also order the reads of x[0]
-    double2 scal = make_double2(0.0, 0.0);
-    if (xnorm2 == 0.0 && alpha.y == 0.0) {
-        tau = make_double2(0.0, 0.0);
-        beta = alpha.x;
-    } else {
-        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
-        tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-        const double2 den = make_double2(alpha.x - beta, alpha.y);
-        const double dd = den.x * den.x + den.y * den.y;
-        scal = make_double2(den.x / dd, -den.y / dd);
+    // the square root and divisions once per block (FP64 division and sqrt are
+    // long instruction sequences on this part), shared through sh[0..5]
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0), scal = make_double2(0.0, 0.0);
+        double b;
+        if (xnorm2 == 0.0 && alpha.y == 0.0) {
+            b = alpha.x;
+        } else {
+            b = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
+            const double ib = 1.0 / b;
+            t = make_double2((b - alpha.x) * ib, -alpha.y * ib);
+            const double2 den = make_double2(alpha.x - b, alpha.y);
+            const double idd = 1.0 / (den.x * den.x + den.y * den.y);
+            scal = make_double2(den.x * idd, -den.y * idd);
+        }
+        sh[0] = t.x;
+        sh[1] = t.y;
+        sh[2] = b;
+        sh[3] = scal.x;
+        sh[4] = scal.y;
     }
+    __syncthreads();
+    tau = make_double2(sh[0], sh[1]);
+    beta = sh[2];
+    const double2 scal = make_double2(sh[3], sh[4]);
     for (int r = threadIdx.x; r < L; r += blockDim.x) x[r] = r == 0 ? make_double2(1.0, 0.0) : c_mul(x[r], scal);
     __syncthreads();
 }
@@ -557,6 +579,7 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
     double2 *sv = s_vw, *sw = s_vw + k, *sn = s_vw + 2 * k;
     const int nb = (int)gridDim.x;
     const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    unsigned int epoch = 0;   // barriers passed so far (same in every thread)
     if (k == 1) {
         if (blockIdx.x == 0 && threadIdx.x == 0) d[0] = a[0].x;
         return;
@@ -591,7 +614,7 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
         }
         if (lane == 0) wbuf[r - 1] = c_mul(ti, make_double2(sx, sy));
     }
-    if (!grid_sync(gs, nb, limit, &s_ok)) return;
+    if (!grid_sync(gs, nb, limit, &s_ok, epoch)) return;
     for (int i = 0; i < k - 1; ++i) {
         L = k - i - 1;
         const double2 *w = wbuf + (i & 1) * k;
@@ -662,7 +685,7 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
             }
             if (lane == 0) wn[r - i - 2] = c_mul(tn, make_double2(sx, sy));
         }
-        if (!grid_sync(gs, nb, limit, &s_ok)) return;
+        if (!grid_sync(gs, nb, limit, &s_ok, epoch)) return;
         double2 *t = sv;
         sv = sn;
         sn = t;
@@ -674,41 +697,80 @@ __global__ void k_house_last(const double2 *a, int k, int ld, double *d) {
     d[k - 1] = a[(size_t)(k - 1) * ld + (k - 1)].x;
 }
 
-// Sturm count: number of eigenvalues of T below x.
-__device__ int sturm_count(const double *d, const double *e2, int k, double x, double pivmin) {
-    int cnt = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0.0) ++cnt;
+// Sturm count: number of eigenvalues of T below x, from the characteristic
+// polynomials of the leading submatrices, p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}
+// (p_{-1} = 1): q_i = p_i / p_{i-1} < 0 exactly when consecutive p change sign, so
+// the count needs no division (three FP64 operations per step).  An exact p_i = 0
+// stands for q_i = 0, which counts as negative (as in the ratio form with a
+// -pivmin pivot): it is replaced by -p_{i-1} 2^-400.  Both p_i and p_{i-1} are
+// multiplied by the same power of two whenever the larger leaves [2^-500, 2^500]
+// (exact; a value that underflows keeps its sign).  Signs are read from the bits.
+__device__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e2, int k, double x) {
+    double pm = 1.0;            // p_{i-1}
+    double p = d[0] - x;        // p_0
+    if (p == 0.0) p = -0x1p-400;
+    int cnt = __double2hiint(p) < 0 ? 1 : 0;
     for (int i = 1; i < k; ++i) {
-        q = d[i] - x - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        if (q < 0.0) ++cnt;
+        double pn = fma(d[i] - x, p, -(e2[i - 1] * pm));
+        const int hn = __double2hiint(pn);
+        if (((hn << 1) | __double2loint(pn)) == 0) pn = -p * 0x1p-400;
+        cnt += (__double2hiint(pn) ^ __double2hiint(p)) < 0 ? 1 : 0;
+        const int ea = (__double2hiint(pn) >> 20) & 0x7FF, eb = (__double2hiint(p) >> 20) & 0x7FF;
+        const int ex = max(ea, eb);
+        if (ex > 1023 + 500 || ex < 1023 - 500) {
+            const double sc = __hiloint2double((2046 - ex) << 20, 0);   // 2^(1023 - ex)
+            pn *= sc;
+            p *= sc;
+        }
+        pm = p;
+        p = pn;
     }
     return cnt;
 }
 
 // scr: [0] tnorm, [1] glo, [2] ghi, [3] pivmin, then e2[k]
+__device__ double block_reduce_max(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+        sh[32] = r;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// Gershgorin bracket, norm and e^2 of T (one CTA).
 __global__ void k_tri_prep(const double *d, const double *e, int k, double *scr) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[33];
     double *e2 = scr + 8;
-    double tn = 0.0, lo = 1e300, hi = -1e300, emax2 = 0.0;
-    for (int i = 0; i < k; ++i) {
+    double tn = 0.0, nlo = -1e300, hi = -1e300, emax2 = 0.0;   // nlo = -min
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double el = i > 0 ? fabs(e[i - 1]) : 0.0;
         const double er = i < k - 1 ? fabs(e[i]) : 0.0;
         tn = fmax(tn, fabs(d[i]) + el + er);
-        lo = fmin(lo, d[i] - el - er);
+        nlo = fmax(nlo, -(d[i] - el - er));
         hi = fmax(hi, d[i] + el + er);
         if (i < k - 1) {
             e2[i] = e[i] * e[i];
             emax2 = fmax(emax2, e2[i]);
         }
     }
-    const double pad = 2.0 * DBL_EPSILON * fmax(tn, 1e-300) + 1e-300;
-    scr[0] = tn;
-    scr[1] = lo - pad;
-    scr[2] = hi + pad;
-    scr[3] = DBL_MIN * fmax(1.0, emax2);
+    tn = block_reduce_max(tn, sh);
+    nlo = block_reduce_max(nlo, sh);
+    hi = block_reduce_max(hi, sh);
+    emax2 = block_reduce_max(emax2, sh);
+    if (threadIdx.x == 0) {
+        const double pad = 2.0 * DBL_EPSILON * fmax(tn, 1e-300) + 1e-300;
+        scr[0] = tn;
+        scr[1] = -nlo - pad;
+        scr[2] = hi + pad;
+        scr[3] = DBL_MIN * fmax(1.0, emax2);
+    }
 }
 
 // Multisection for the lowest nkeep eigenvalues of T, one warp per eigenvalue
@@ -722,11 +784,10 @@ __global__ void k_bisect(const double *d, int k, int nkeep, const double *scr, d
     if (j >= nkeep) return;   // whole warps exit together (j is uniform per warp)
     const double *e2 = scr + 8;
     double lo = scr[1], hi = scr[2];
-    const double pivmin = scr[3];
     for (int round = 0; round < 40; ++round) {
         if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
         const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-        const int c = sturm_count(d, e2, k, x, pivmin);
+        const int c = sturm_count(d, e2, k, x);
         const unsigned ball = __ballot_sync(0xffffffffu, c > j);
         const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
         if (ball == 0u) {
@@ -750,7 +811,7 @@ __device__ __forceinline__ double hash_uniform(unsigned long long x) {
     return ((double)(x >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
 }
 
-// Inverse iteration for eigenvalue j: three solves of (T - lam_j I) y = x with
+// Inverse iteration for eigenvalue j: two solves of (T - lam_j I) y = x with
 // partial pivoting (row interchanges), normalising after each solve; the
 // start vector is a fixed pseudo-random one.  Vector j goes to zt[j][0..k).
 // One warp per eigenvalue (one CTA each, so the eigenvalues spread over the
@@ -806,7 +867,7 @@ k_inverse_iter(const double *d, const double *e, int k, int nkeep, const double 
         D[i] = 1.0 / di;
     }
     __syncwarp();
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 2; ++it) {
         if (lane == 0) {
             for (int i = 0; i < k - 1; ++i) {
                 if (F[i] != 0.0) {
@@ -884,7 +945,7 @@ __global__ void k_backtransform(int k, const double2 *__restrict__ vh, int ldv,
                                 const double2 *__restrict__ tau, const double *__restrict__ zt,
                                 double2 *z, int ldz) {
     extern __shared__ double2 sz[];
-    __shared__ double sh[33];
+    __shared__ double2 sh2[33];
     const int j = blockIdx.x;
     for (int r = threadIdx.x; r < k; r += blockDim.x) sz[r] = make_double2(zt[(size_t)j * k + r], 0.0);
     __syncthreads();
@@ -892,15 +953,14 @@ __global__ void k_backtransform(int k, const double2 *__restrict__ vh, int ldv,
         const double2 t = tau[i];
         if (t.x == 0.0 && t.y == 0.0) continue;
         const double2 *v = vh + (size_t)i * ldv;
-        double sx = 0.0, sy = 0.0;
+        double2 acc = make_double2(0.0, 0.0);
         for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
             const double2 p = c_mul(c_conj(v[r]), sz[r]);
-            sx += p.x;
-            sy += p.y;
+            acc.x += p.x;
+            acc.y += p.y;
         }
-        sx = block_sum(sx, sh);
-        sy = block_sum(sy, sh);
-        const double2 f = c_mul(t, make_double2(sx, sy));
+        acc = block_sum_c(acc, sh2);
+        const double2 f = c_mul(t, acc);
         for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
             const double2 p = c_mul(f, v[r]);
             sz[r].x -= p.x;
@@ -977,7 +1037,7 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         count_launch(ctx);
     }
     RS_LAUNCHED(ctx, "householder");
-    k_tri_prep<<<1, 1, 0, st>>>(w.d, w.e, k, w.dscr);
+    k_tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.dscr);
     count_launch(ctx);
     // one warp per eigenvalue and one CTA per warp: the Sturm counts and the
     // substitutions are FP64 chains, so the eigenvalues spread over the SMs

@@ -339,6 +339,219 @@ __global__ void k_gram_tc_reduce(const float *__restrict__ part, int splits, int
     g[(size_t)i * ld + j] = make_double2(scale * re, scale * im);
 }
 
+
+// ---- Ritz rotation: out[b][:] = sum_j C[j][b] Y[j][:] ------------------------------
+// As a real GEMM D[p][q] = sum_j A[p][j] B[j][q] with p the interleaved real index
+// of a grid point (M, 2n), j the row of Y (K) and q in [0, 2 nh) (N): the first nh
+// columns of B hold Re C[j][b], the next nh Im C[j][b].  Then for the pair of rows
+// (re, im) of one point, out_re = D[re][b] - D[im][nh + b] and
+// out_im = D[im][b] + D[re][nh + b]; the epilogue forms them with one shuffle.
+// A is Y itself, read MN-major (the grid index is contiguous, K runs over rows);
+// B is the small coefficient matrix, K-major.  Per 128-row tile the [W P] rows
+// are accumulated first and written as the new P, then the X rows accumulate on
+// top and the sum is written as the new X (= X C_X + P).
+constexpr int RBK = 64;               // K rows (of Y) per pipeline stage
+constexpr int RSTAGES = 2;
+constexpr int RTHREADS = 192;         // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int RA_CHUNK = 64 * RBK * 2;  // one 64-column chunk of A: 8 KB
+constexpr int MAX_NH = 240;
+
+__host__ __device__ constexpr int rot_stage_bytes(int nh) { return 4 * RA_CHUNK + 4 * nh * 128; }
+
+// Shared-memory descriptor of an MN-major operand with 128-byte swizzle: 64
+// contiguous MN elements per 128-byte row, 8 K-rows per 1024-byte group; lbo =
+// byte distance between 64-element MN chunks, sbo = between 8-row K groups.
+__device__ __forceinline__ uint64_t smem_desc_mn(const void *p, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (smem_u32(p) & 0x3FFFFu) >> 4;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Split C (FP64 complex, rows j0..j0+nrows of [k][ldc], m columns) into the K-major
+// bf16 hi/lo operand [2 nh][kpad]: row q < nh is Re C[j0 + t][q], row nh + q is
+// Im C[j0 + t][q] at column t; zero outside (t >= nrows or q >= m).
+__global__ void k_rot_coef(const double2 *__restrict__ c, int ldc, int j0, int nrows, int m, int nh,
+                           int kpad, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2LL * nh * kpad) return;
+    const int row = (int)(idx / kpad), t = (int)(idx % kpad);
+    const int q = row < nh ? row : row - nh;
+    float v = 0.0f;
+    if (t < nrows && q < m) {
+        const double2 z = c[(size_t)(j0 + t) * ldc + q];
+        v = (float)(row < nh ? z.x : z.y);
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(RTHREADS, 1)
+k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUtensorMap mWPl,
+         const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+         const __grid_constant__ CUtensorMap mBWPh, const __grid_constant__ CUtensorMap mBWPl,
+         const __grid_constant__ CUtensorMap mBXh, const __grid_constant__ CUtensorMap mBXl, int nh,
+         int m, int kb_wp, int kb_x, long long two_n, int ntiles, float *__restrict__ out0,
+         float *__restrict__ out1, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[RSTAGES];
+    __shared__ __align__(8) uint64_t empty_bar[RSTAGES];
+    __shared__ __align__(8) uint64_t accf_bar;   // accumulator ready (MMA -> epilogue)
+    __shared__ __align__(8) uint64_t acce_bar;   // accumulator drained (epilogue -> MMA)
+    __shared__ __align__(8) uint64_t done_bar;   // every MMA issued has completed
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int stage_bytes = rot_stage_bytes(nh);
+    const int bpart = nh * 128;               // one half (re or im) of B hi or lo
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RSTAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&accf_bar, 1);
+        mbar_init(&acce_bar, 4);
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int *abort = &s_abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer: k-blocks of ([W P] rows, then X rows) for each tile
+        int it = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            const int m0 = t * 128;
+            for (int ph = 0; ph < 2 && !stop; ++ph) {
+                const int nkb = ph == 0 ? kb_wp : kb_x;
+                const CUtensorMap *ah = ph == 0 ? &mWPh : &mXh, *al = ph == 0 ? &mWPl : &mXl;
+                const CUtensorMap *bh = ph == 0 ? &mBWPh : &mBXh, *bl = ph == 0 ? &mBWPl : &mBXl;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % RSTAGES, r = it / RSTAGES;
+                    if (r > 0 && !mbar_wait(&empty_bar[s], (r - 1) & 1, abort)) { stop = true; break; }
+                    unsigned char *st = smem + s * stage_bytes;
+                    mbar_expect_tx(&full_bar[s], stage_bytes);
+                    const int y = kb * RBK;
+                    tma_load_2d(st, ah, &full_bar[s], m0, y);
+                    tma_load_2d(st + RA_CHUNK, ah, &full_bar[s], m0 + 64, y);
+                    tma_load_2d(st + 2 * RA_CHUNK, al, &full_bar[s], m0, y);
+                    tma_load_2d(st + 3 * RA_CHUNK, al, &full_bar[s], m0 + 64, y);
+                    unsigned char *sb = st + 4 * RA_CHUNK;
+                    tma_load_2d(sb, bh, &full_bar[s], y, 0);
+                    tma_load_2d(sb + bpart, bh, &full_bar[s], y, nh);
+                    tma_load_2d(sb + 2 * bpart, bl, &full_bar[s], y, 0);
+                    tma_load_2d(sb + 3 * bpart, bl, &full_bar[s], y, nh);
+                }
+            }
+        }
+        if (*abort) {
+            // let the copies still in flight land before the CTA leaves
+            for (int j = max(0, it - RSTAGES); j < it; ++j) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full_bar[j % RSTAGES], (j / RSTAGES) & 1) && clock64() - t0 < WAIT_LIMIT) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = idesc_bf16(128, nh) | (1u << 15);   // A MN-major
+        int it = 0, ap = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            for (int ph = 0; ph < 2 && !stop; ++ph) {
+                if (ap > 0 && !mbar_wait(&acce_bar, (ap - 1) & 1, abort)) { stop = true; break; }
+                tc_fence_after();
+                const int nkb = ph == 0 ? kb_wp : kb_x;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % RSTAGES, r = it / RSTAGES;
+                    if (!mbar_wait(&full_bar[s], r & 1, abort)) { stop = true; break; }
+                    tc_fence_after();
+                    unsigned char *st = smem + s * stage_bytes;
+                    unsigned char *sb = st + 4 * RA_CHUNK;
+#pragma unroll
+                    for (int kk = 0; kk < RBK / 16; ++kk) {
+                        // A: 16 K-rows = two 8-row groups of 1024 B; B: 16 bf16 = 32 B
+                        const uint64_t ah = smem_desc_mn(st + kk * 2048, RA_CHUNK, 1024);
+                        const uint64_t al = smem_desc_mn(st + 2 * RA_CHUNK + kk * 2048, RA_CHUNK, 1024);
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const uint64_t bh = smem_desc(sb + half * bpart + kk * 32);
+                            const uint64_t bl = smem_desc(sb + (2 + half) * bpart + kk * 32);
+                            const uint32_t d = tmem + (uint32_t)(half * nh);
+                            const uint32_t acc = (ph == 0 && kb == 0 && kk == 0) ? 0u : 1u;
+                            mma_bf16(d, ah, bh, idesc, acc);
+                            mma_bf16(d, ah, bl, idesc, 1u);
+                            mma_bf16(d, al, bh, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
+                }
+                if (stop) break;
+                mma_commit(&accf_bar);
+                ++ap;
+            }
+        }
+        // every MMA issued so far must finish before TMEM is released (bounded)
+        mma_commit(&done_bar);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&done_bar, 0)) {
+            if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; break; }
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp & 3;
+        int ap = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const long long m0 = (long long)t * 128;
+            for (int ph = 0; ph < 2; ++ph) {
+                if (!mbar_wait(&accf_bar, ap & 1, abort)) break;
+                tc_fence_after();
+                float *out = ph == 0 ? out1 : out0;
+                const long long p = m0 + q * 32 + lane;
+                for (int b0 = 0; b0 < m; b0 += 32) {
+                    float vr[32], vi[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b0, vr);
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(nh + b0), vi);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float pv = __shfl_xor_sync(0xffffffffu, vi[i], 1);
+                        const float v = (lane & 1) ? vr[i] + pv : vr[i] - pv;
+                        if (out && b0 + i < m && p < two_n) out[(size_t)(b0 + i) * two_n + p] = v;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce_bar);
+                ++ap;
+            }
+            if (*abort) break;
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && *abort) atomicExch(err, 1);
+}
 }  // namespace tc
 }  // namespace rsdft
 
@@ -361,14 +574,15 @@ static rsdft_status encoder(rsdft_ctx *ctx) {
     return RSDFT_OK;
 }
 
-// 2D BF16 operand [rows][ldk] with kvalid valid columns; box 64 x 128, 128-byte swizzle.
+// 2D BF16 operand [rows][ldk] with kvalid valid columns; box 64 x box_rows,
+// 128-byte swizzle (rows beyond `rows` and columns beyond kvalid read as zero).
 static rsdft_status make_map(rsdft_ctx *ctx, CUtensorMap *m, const void *base, long long kvalid,
-                             int rows, long long ldk) {
+                             int rows, long long ldk, int box_rows = BM) {
     if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((ldk * 2) & 15))
         return fail(ctx, RSDFT_E_INVALID, "tensor map base or stride not 16-byte aligned");
     cuuint64_t dims[2] = {(cuuint64_t)kvalid, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ldk * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -487,17 +701,96 @@ static rsdft_status check_err(rsdft_ctx *ctx, cudaStream_t st) {
     return RSDFT_OK;
 }
 
+// Coefficient operands of one rotation: [W P] part and X part, hi and lo.
+struct RotCoef {
+    __nv_bfloat16 *wph, *wpl, *xh, *xl;
+    int kpad_wp, kpad_x;
+};
+
+static rsdft_status rot_coef(rsdft_ctx *ctx, const double2 *c, int ldc, int k, int m, int nh, RotCoef &rc,
+                             cudaStream_t st) {
+    Workspace &w = ctx->ws;
+    rc.kpad_wp = cdiv(k - m, RBK) * RBK;
+    rc.kpad_x = cdiv(m, RBK) * RBK;
+    const size_t per_wp = (size_t)2 * nh * rc.kpad_wp, per_x = (size_t)2 * nh * rc.kpad_x;
+    const size_t need = 2 * (per_wp + per_x) * sizeof(__nv_bfloat16) + 256;
+    if (need > w.tcrot_bytes) {
+        if (w.tcrot) {
+            cudaFree(w.tcrot);
+            for (auto &p : ctx->owned)
+                if (p == w.tcrot) p = nullptr;
+        }
+        w.tcrot = nullptr;
+        w.tcrot_bytes = 0;
+        RS_TRY(dev_alloc(ctx, &w.tcrot, need));
+        w.tcrot_bytes = need;
+    }
+    rc.wph = reinterpret_cast<__nv_bfloat16 *>(w.tcrot);
+    rc.wpl = rc.wph + per_wp;
+    rc.xh = rc.wpl + per_wp;
+    rc.xl = rc.xh + per_x;
+    k_rot_coef<<<cdiv((long long)per_wp, 256), 256, 0, st>>>(c, ldc, m, k - m, m, nh, rc.kpad_wp, rc.wph, rc.wpl);
+    k_rot_coef<<<cdiv((long long)per_x, 256), 256, 0, st>>>(c, ldc, 0, m, m, nh, rc.kpad_x, rc.xh, rc.xl);
+    count_launch(ctx, 2);
+    RS_LAUNCHED(ctx, "k_rot_coef");
+    return RSDFT_OK;
+}
+
+// out0 = Y C, out1 = Y[m:k] C[m:k] with Y the split rows row0 .. row0 + k of b.
+static rsdft_status rotate_launch(rsdft_ctx *ctx, const Buffers &b, int row0, int k, const double2 *c, int ldc,
+                                  int m, float2 *out0, float2 *out1, cudaStream_t st) {
+    RS_TRY(encoder(ctx));
+    const int nh = cdiv(m, 16) * 16;
+    RotCoef rc;
+    RS_TRY(rot_coef(ctx, c, ldc, k, m, nh, rc, st));
+    const long long two_n = 2 * ctx->n;
+    CUtensorMap mWPh, mWPl, mXh, mXl, mBWPh, mBWPl, mBXh, mBXl;
+    const size_t off_wp = (size_t)(row0 + m) * b.ldk, off_x = (size_t)row0 * b.ldk;
+    RS_TRY(make_map(ctx, &mWPh, b.bh + off_wp, two_n, k - m, b.ldk, RBK));
+    RS_TRY(make_map(ctx, &mWPl, b.bl + off_wp, two_n, k - m, b.ldk, RBK));
+    RS_TRY(make_map(ctx, &mXh, b.bh + off_x, two_n, m, b.ldk, RBK));
+    RS_TRY(make_map(ctx, &mXl, b.bl + off_x, two_n, m, b.ldk, RBK));
+    RS_TRY(make_map(ctx, &mBWPh, rc.wph, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
+    RS_TRY(make_map(ctx, &mBWPl, rc.wpl, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
+    RS_TRY(make_map(ctx, &mBXh, rc.xh, rc.kpad_x, 2 * nh, rc.kpad_x, nh));
+    RS_TRY(make_map(ctx, &mBXl, rc.xl, rc.kpad_x, 2 * nh, rc.kpad_x, nh));
+    RS_TRY(partials(ctx, 0));
+    RS_CUDA(ctx, cudaMemsetAsync(ctx->ws.tcerr, 0, sizeof(int), st));
+    const int smem = RSTAGES * rot_stage_bytes(nh) + 1024;
+    static int attr = 0;
+    if (attr < smem) {
+        RS_CUDA(ctx, cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = smem;
+    }
+    const int ntiles = (int)((two_n + 127) / 128);
+    const int grid = std::min(ntiles, ctx->num_sms);
+    {
+        ProfScope ps(ctx, RSDFT_K_ROTATE_TC, 3.0 * 2.0 * (double)two_n * (2.0 * m) * k,
+                     2.0 * 2.0 * (double)k * two_n + 2.0 * 4.0 * (double)m * two_n, st);
+        k_rot_tc<<<grid, RTHREADS, smem, st>>>(mWPh, mWPl, mXh, mXl, mBWPh, mBWPl, mBXh, mBXl, nh, m,
+                                                rc.kpad_wp / RBK, rc.kpad_x / RBK, two_n, ntiles,
+                                                reinterpret_cast<float *>(out0),
+                                                reinterpret_cast<float *>(out1), ctx->ws.tcerr);
+    }
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_rot_tc");
+    return check_err(ctx, st);
+}
+
 }  // namespace tc
 
 // G_S = <Y|Y>, G_H = <Y|HY> (Hermitised, scaled by dV) for FP32 blocks on the
-// tensor cores: one GEMM of A = Y against B = [Y; Yrot; HY; HYrot].
+// tensor cores: one GEMM of A = Y against B = [Y; Yrot; HY; HYrot] (A is read
+// from the first k rows of B).  The split rows stay in the workspace for the
+// Ritz rotation (rotate_tc_split).
 rsdft_status gram_tc_sh(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const RowBlocksT<float2> &HY,
                         double2 *gs, double2 *gh, int ld, cudaStream_t st) {
     const int k = Y.cnt[0] + Y.cnt[1] + Y.cnt[2];
     if (k <= 0) return RSDFT_OK;
     tc::Buffers b;
-    RS_TRY(tc::buffers(ctx, k, 4 * k, b));
-    RS_TRY(tc::split_rows(ctx, Y, 0, b.ah, b.al, 0, b.ldk, st));
+    RS_TRY(tc::buffers(ctx, 0, 4 * k, b));
+    b.ah = b.bh;   // A = the first k rows of B
+    b.al = b.bl;
     RS_TRY(tc::split_rows(ctx, Y, 0, b.bh, b.bl, 0, b.ldk, st));
     RS_TRY(tc::split_rows(ctx, Y, 1, b.bh, b.bl, k, b.ldk, st));
     RS_TRY(tc::split_rows(ctx, HY, 0, b.bh, b.bl, 2 * k, b.ldk, st));
@@ -530,6 +823,26 @@ rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlock
     return tc::check_err(ctx, st);
 }
 
+bool rotate_tc_fits(int k, int m) { return m >= 1 && k > m && cdiv(m, 16) * 16 <= tc::MAX_NH; }
+
+rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
+                             float2 *out0, float2 *out1, cudaStream_t st) {
+    if (!rotate_tc_fits(k, m)) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
+    tc::Buffers b;
+    RS_TRY(tc::buffers(ctx, 0, 4 * k, b));   // the layout gram_tc_sh wrote
+    return tc::rotate_launch(ctx, b, which == 0 ? 0 : 2 * k, k, c, ldc, m, out0, out1, st);
+}
+
+rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c, int ldc, int m,
+                       float2 *out0, float2 *out1, cudaStream_t st) {
+    if (!rotate_tc_fits(k, m)) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
+    tc::Buffers b;
+    RS_TRY(tc::buffers(ctx, 0, k, b));
+    RowBlocksT<float2> Y{{y, nullptr, nullptr}, {k, 0, 0}};
+    RS_TRY(tc::split_rows(ctx, Y, 0, b.bh, b.bl, 0, b.ldk, st));
+    return tc::rotate_launch(ctx, b, 0, k, c, ldc, m, out0, out1, st);
+}
+
 }  // namespace rsdft
 
 using namespace rsdft;
@@ -543,4 +856,14 @@ extern "C" rsdft_status rsdft_gram_bf16x3(rsdft_ctx *ctx, const void *a_dev, int
     RowBlocksT<float2> A{{(const float2 *)a_dev, nullptr, nullptr}, {na, 0, 0}};
     RowBlocksT<float2> B{{(const float2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
     return gram_tc(ctx, A, B, (double2 *)g_dev, nb, as_stream(stream));
+}
+
+extern "C" rsdft_status rsdft_rotate_bf16x3(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
+                                            void *out0_dev, void *out1_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (!y_dev || !c_dev || !out0_dev || !out1_dev) return fail(ctx, RSDFT_E_INVALID, "NULL pointer");
+    if (!rotate_tc_fits(k, m)) return fail(ctx, RSDFT_E_INVALID, "rotation shape k %d, m %d unsupported", k, m);
+    RS_TRY(ensure_workspace(ctx, 1));
+    return rotate_tc(ctx, (const float2 *)y_dev, k, (const double2 *)c_dev, m, m, (float2 *)out0_dev,
+                     (float2 *)out1_dev, as_stream(stream));
 }

@@ -48,29 +48,145 @@ __device__ __forceinline__ double block_sum2(double v, double *sh) {
     return sh[32];
 }
 
-// res[b] = ||hx_b - theta_b x_b|| (dV metric, FP64 sums); vexp[b] = <x_b|V|x_b>
+// Row reductions over slices: grid (S, rows), each CTA sums one slice of one row
+// into part[row][S]; a small kernel finishes the sums.  FP64 blocks accumulate in
+// FP64; FP32 blocks (mixed form) form each term in FP32, add runs of 32 terms in
+// FP32 and the run sums in FP64 (relative error ~1e-6 on the norm), which keeps
+// the FP64 pipe out of the inner loop.
+__device__ __forceinline__ void slice_of(long long n, int S, int s, long long &i0, long long &i1) {
+    const long long c = (n + S - 1) / S;
+    i0 = (long long)s * c;
+    i1 = i0 + c < n ? i0 + c : n;
+}
+
+// part[b][s] = (sum |hx_b - theta_b x_b|^2, sum V |x_b|^2) over slice s
 template <typename V>
 __global__ void __launch_bounds__(RTHREADS)
-k_resid(const V *__restrict__ hx, const V *__restrict__ x, const double *__restrict__ theta,
-        const double *__restrict__ v, long long n, double dV, double *res, double *vexp) {
+k_resid_part(const V *__restrict__ hx, const V *__restrict__ x, const double *__restrict__ theta,
+             const double *__restrict__ v64, const float *__restrict__ v32, long long n, int S,
+             double2 *__restrict__ part) {
     __shared__ double sh[33];
-    const int b = blockIdx.x;
-    const double th = theta[b];
+    const int s_ = blockIdx.x, b = blockIdx.y;
+    long long i0, i1;
+    slice_of(n, S, s_, i0, i1);
     const V *h = hx + (size_t)b * n, *xx = x + (size_t)b * n;
     double s = 0.0, sv = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const V a = h[i], c = xx[i];
-        const double cx = (double)c.x, cy = (double)c.y;
-        const double rx = (double)a.x - th * cx, ry = (double)a.y - th * cy;
-        s += rx * rx + ry * ry;
-        sv += v[i] * (cx * cx + cy * cy);
+    if constexpr (std::is_same<V, float2>::value) {
+        const float th = (float)theta[b];
+        float a32 = 0.0f, v32s = 0.0f;
+        int cnt = 0;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const float2 a = h[i], c = xx[i];
+            const float rx = a.x - th * c.x, ry = a.y - th * c.y;
+            a32 += rx * rx + ry * ry;
+            v32s += v32[i] * (c.x * c.x + c.y * c.y);
+            if (++cnt == 32) {
+                s += a32;
+                sv += v32s;
+                a32 = v32s = 0.0f;
+                cnt = 0;
+            }
+        }
+        s += a32;
+        sv += v32s;
+    } else {
+        const double th = theta[b];
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const V a = h[i], c = xx[i];
+            const double rx = a.x - th * c.x, ry = a.y - th * c.y;
+            s += rx * rx + ry * ry;
+            sv += v64[i] * (c.x * c.x + c.y * c.y);
+        }
     }
     s = block_sum2(s, sh);
     sv = block_sum2(sv, sh);
-    if (threadIdx.x == 0) {
-        res[b] = sqrt(s * dV);
-        vexp[b] = sv * dV;
+    if (threadIdx.x == 0) part[(size_t)b * S + s_] = make_double2(s, sv);
+}
+
+// res[b] = ||hx_b - theta_b x_b|| (dV metric); vexp[b] = <x_b|V|x_b>
+__global__ void k_resid_fin(const double2 *__restrict__ part, int S, int m, double dV, double *res,
+                            double *vexp) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    double s = 0.0, sv = 0.0;
+    for (int q = 0; q < S; ++q) {
+        s += part[(size_t)b * S + q].x;
+        sv += part[(size_t)b * S + q].y;
     }
+    res[b] = sqrt(s * dV);
+    vexp[b] = sv * dV;
+}
+
+// part[b][s] = sum |a_b|^2 over slice s
+template <typename V>
+__global__ void __launch_bounds__(RTHREADS)
+k_rownorm_part(const V *__restrict__ a, long long n, int S, double *__restrict__ part) {
+    __shared__ double sh[33];
+    const int s_ = blockIdx.x, b = blockIdx.y;
+    long long i0, i1;
+    slice_of(n, S, s_, i0, i1);
+    const V *r = a + (size_t)b * n;
+    double s = 0.0;
+    if constexpr (std::is_same<V, float2>::value) {
+        float a32 = 0.0f;
+        int cnt = 0;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const float2 v = r[i];
+            a32 += v.x * v.x + v.y * v.y;
+            if (++cnt == 32) {
+                s += a32;
+                a32 = 0.0f;
+                cnt = 0;
+            }
+        }
+        s += a32;
+    } else {
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double x = r[i].x, y = r[i].y;
+            s += x * x + y * y;
+        }
+    }
+    s = block_sum2(s, sh);
+    if (threadIdx.x == 0) part[(size_t)b * S + s_] = s;
+}
+
+__global__ void k_rownorm_fin(const double *__restrict__ part, int S, int rows, double dV, double *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= rows) return;
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += part[(size_t)b * S + q];
+    out[b] = sqrt(s * dV);
+}
+
+// slices per row: about 8 CTAs per SM in total, slices of at least 4096 points
+static int row_slices(const rsdft_ctx *ctx, int rows) {
+    const int want = cdiv(8 * ctx->num_sms, std::max(rows, 1));
+    const int most = (int)std::max(1LL, ctx->n / 4096);
+    return std::max(1, std::min(std::min(want, most), 64));
+}
+
+template <typename V>
+static rsdft_status resid_norms(rsdft_ctx *ctx, const V *hx, const V *x, int m, cudaStream_t st) {
+    Workspace &w = ctx->ws;
+    const int S = row_slices(ctx, m);
+    double2 *part = w.gram_part;   // free between Gram calls
+    k_resid_part<V><<<dim3(S, m), RTHREADS, 0, st>>>(hx, x, w.theta, ctx->v, ctx->v32, ctx->n, S, part);
+    k_resid_fin<<<cdiv(m, 128), 128, 0, st>>>(part, S, m, ctx->dV, w.res, w.vexp);
+    count_launch(ctx, 2);
+    RS_LAUNCHED(ctx, "k_resid");
+    return RSDFT_OK;
+}
+
+template <typename V>
+static rsdft_status row_norms(rsdft_ctx *ctx, const V *a, int rows, double *out, cudaStream_t st) {
+    if (rows <= 0) return RSDFT_OK;
+    const int S = row_slices(ctx, rows);
+    double *part = reinterpret_cast<double *>(ctx->ws.gram_part);
+    k_rownorm_part<V><<<dim3(S, rows), RTHREADS, 0, st>>>(a, ctx->n, S, part);
+    k_rownorm_fin<<<cdiv(rows, 128), 128, 0, st>>>(part, S, rows, ctx->dV, out);
+    count_launch(ctx, 2);
+    RS_LAUNCHED(ctx, "k_rownorm");
+    return RSDFT_OK;
 }
 
 // t_b = <x_b|T|x_b> = theta_b - <x_b|V|x_b> - sum_aj E_aj |<beta_aj|x_b>|^2, for the
@@ -89,21 +205,6 @@ __global__ void k_tkin(const double *__restrict__ theta, const double *__restric
         nl += pt.e_kb[q] * ((double)c.x * c.x + (double)c.y * c.y);
     }
     tkin[j] = theta[b] - vexp[b] - nl;
-}
-
-template <typename V>
-__global__ void __launch_bounds__(RTHREADS)
-k_rownorm(const V *__restrict__ a, long long n, double dV, double *out) {
-    __shared__ double sh[33];
-    const int b = blockIdx.x;
-    const V *r = a + (size_t)b * n;
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const double x = r[i].x, y = r[i].y;
-        s += x * x + y * y;
-    }
-    s = block_sum2(s, sh);
-    if (threadIdx.x == 0) out[b] = sqrt(s * dV);
 }
 
 // a[b] /= nrm[b] and (optionally) a2[b] /= nrm[b]
@@ -222,10 +323,7 @@ template <> struct Ops<float2> {
 
 rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st) {
     if (nb <= 0) return RSDFT_OK;
-    k_rownorm<double2><<<nb, RTHREADS, 0, st>>>(a, ctx->n, ctx->dV, out);
-    count_launch(ctx);
-    RS_LAUNCHED(ctx, "k_rownorm");
-    return RSDFT_OK;
+    return row_norms<double2>(ctx, a, nb, out, st);
 }
 
 // Per-phase CUDA-event timing of one iteration.
@@ -297,7 +395,8 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
     int *hactp = reinterpret_cast<int *>(w.hbuf + 3 * m);  // P columns kept
     int *actp = w.act + m;
     const bool fp32 = sizeof(V) == sizeof(float2);
-    const bool tc = fp32 && o.tensor_cores != 0;
+    const bool tc = fp32 && o.tensor_cores >= 1;       // Gram matrices on tcgen05
+    const bool tc_rot = fp32 && o.tensor_cores >= 2;   // and the Ritz rotations
     const double pivot_tol = fp32 ? std::max(o.pivot_tol, PIVOT_TOL_FP32) : o.pivot_tol;
     const double lock_tol = fp32 ? std::max(o.lock_tol, LOCK_TOL_FP32) : o.lock_tol;
     const double p_drop = fp32 ? P_DROP_FP32 : 0.0;
@@ -322,14 +421,10 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
     double prev = -1.0;
     rsdft_status result = RSDFT_OK;
     for (;;) {
-        k_resid<V><<<m, RTHREADS, 0, st>>>(HX, X, w.theta, ctx->v, n, dV, w.res, w.vexp);
-        count_launch(ctx);
-        RS_LAUNCHED(ctx, "k_resid");
+        RS_TRY(resid_norms<V>(ctx, HX, X, m, st));
         RS_CUDA(ctx, cudaMemcpyAsync(hres, w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (haveP && p_drop > 0.0) {
-            k_rownorm<V><<<m, RTHREADS, 0, st>>>(P, n, dV, w.nrm);
-            count_launch(ctx);
-            RS_LAUNCHED(ctx, "k_rownorm P");
+            RS_TRY(row_norms<V>(ctx, P, m, w.nrm, st));
             RS_CUDA(ctx, cudaMemcpyAsync(hpn, w.nrm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         }
         RS_CUDA(ctx, cudaStreamSynchronize(st));
@@ -389,16 +484,16 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[1], st));
         RS_TRY(Ops<V>::apply_h(ctx, W, HW, na, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[2], st));
-        k_rownorm<V><<<na, RTHREADS, 0, st>>>(W, n, dV, w.nrm);
+        RS_TRY(row_norms<V>(ctx, W, na, w.nrm, st));
         k_scale_rows<V><<<rowgrid, 256, 0, st>>>(W, HW, n, w.nrm);
-        count_launch(ctx, 2);
+        count_launch(ctx);
         RS_LAUNCHED(ctx, "normalise W");
         if (np_ > 0) {
             const dim3 pgrid(rowgrid.x, np_);
             k_gather_rows<V><<<pgrid, 256, 0, st>>>(P, HP, actp, n, Pn, HPn);
-            k_rownorm<V><<<np_, RTHREADS, 0, st>>>(Pn, n, dV, w.nrm);
+            RS_TRY(row_norms<V>(ctx, Pn, np_, w.nrm, st));
             k_scale_rows<V><<<pgrid, 256, 0, st>>>(Pn, HPn, n, w.nrm);
-            count_launch(ctx, 3);
+            count_launch(ctx, 2);
             RS_LAUNCHED(ctx, "normalise P");
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[3], st));
@@ -411,8 +506,19 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
         rs.dropped += nd;
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[5], st));
-        RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, P, st));
-        RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, HP, st));
+        bool rotated = false;
+        if constexpr (std::is_same<V, float2>::value) {
+            // the split-BF16 rows of Y and HY are still in the workspace from the Gram
+            if (tc_rot && rotate_tc_fits(k, m)) {
+                RS_TRY(rotate_tc_split(ctx, 0, k, w.Cfull, m, m, Xn, P, st));
+                RS_TRY(rotate_tc_split(ctx, 1, k, w.Cfull, m, m, HXn, HP, st));
+                rotated = true;
+            }
+        }
+        if (!rotated) {
+            RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, P, st));
+            RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, HP, st));
+        }
         if (stats) {
             RS_CUDA(ctx, cudaEventRecord(pe.ev[6], st));
             pe.pending = true;

@@ -73,6 +73,7 @@ struct Workspace {
     void *tcbuf = nullptr;  size_t tc_bytes = 0;
     float *tcpart = nullptr;  size_t tcpart_elems = 0;
     int *tcerr = nullptr;
+    void *tcrot = nullptr;  size_t tcrot_bytes = 0;   // split rotation coefficients
     // per-band vectors [cap_band]
     double *theta = nullptr, *res = nullptr, *vexp = nullptr, *tkin = nullptr, *nrm = nullptr;
     int *act = nullptr;      // [active bands (m) | P columns kept (m)]
@@ -224,6 +225,16 @@ rsdft_status gram_tc_sh(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const RowBl
                         double2 *gs, double2 *gh, int ld, cudaStream_t st);
 rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
                      double2 *g, int ld, cudaStream_t st);
+// Ritz rotation on the tensor cores from the split-BF16 rows that the last
+// gram_tc_sh left in the workspace (which = 0: Y, which = 1: HY):
+// out0 = Y C (all k rows), out1 = Y[m:k] C[m:k] (the new P).  rotate_tc_fits
+// says whether the shape is supported (m <= 240).
+bool rotate_tc_fits(int k, int m);
+rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
+                             float2 *out0, float2 *out1, cudaStream_t st);
+// Same for an arbitrary FP32 block y [k][n] (splits it first).
+rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c, int ldc, int m,
+                       float2 *out0, float2 *out1, cudaStream_t st);
 
 // ---- dense core (dense.cu) ----------------------------------------------------
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,

@@ -474,6 +474,7 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
         out->free_energy = out->e_tot - opts->kT * occ2[1];
         out->drho = drho;
         out->lobpcg_iterations = ls.iterations;
+        out->lobpcg_iterations_mixed = ls.iterations_mixed;
         out->step = s.step;
     }
     s.step++;

@@ -73,7 +73,8 @@ class ScfOut(C.Structure):
     _fields_ = [("e_tot", C.c_double), ("free_energy", C.c_double), ("e_band", C.c_double),
                 ("e_h", C.c_double), ("e_xc", C.c_double), ("e_vxc", C.c_double),
                 ("mu", C.c_double), ("entropy", C.c_double), ("drho", C.c_double),
-                ("lobpcg_iterations", C.c_int), ("step", C.c_int)]
+                ("lobpcg_iterations", C.c_int), ("lobpcg_iterations_mixed", C.c_int),
+                ("step", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -95,6 +96,7 @@ _PROTOS = {
     "rsdft_gram": (ip, [vp, vp, ip, vp, ip, vp, vp]),
     "rsdft_gram_static": (ip, [vp, ip, vp, ip, C.c_longlong, dp, vp, vp]),
     "rsdft_gram_bf16x3": (ip, [vp, vp, ip, vp, ip, vp, vp]),
+    "rsdft_rotate_bf16x3": (ip, [vp, vp, ip, vp, ip, vp, vp, vp]),
     "rsdft_rotate": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_rayleigh_ritz": (ip, [vp, vp, vp, ip, ip, dp, vp, vp, vp, vp]),
     "rsdft_eigh": (ip, [vp, vp, ip, ip, vp, vp, vp]),
@@ -114,7 +116,8 @@ _PROTOS = {
 }
 
 K_GRAM, K_ROTATE, K_FFT_XY_FWD, K_FFT_Z, K_FFT_XY_INV, K_PROJECT, K_DENSE, K_GRAM_TC = range(8)
-KERNEL_NAMES = ["gram", "rotate", "fft_xy_fwd", "fft_z", "fft_xy_inv", "project", "dense", "gram_tc"]
+KERNEL_NAMES = ["gram", "rotate", "fft_xy_fwd", "fft_z", "fft_xy_inv", "project", "dense", "gram_tc",
+                "rotate_tc"]
 
 
 def lib() -> C.CDLL:
@@ -271,6 +274,11 @@ class Context:
     def gram_bf16x3(self, a, b, g):
         self._check(lib().rsdft_gram_bf16x3(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0],
                                             _ptr(g), _stream()))
+
+    def rotate_bf16x3(self, y, c, out0, out1):
+        """rsdft_rotate_bf16x3: out1 = C[m:]^T Y[m:], out0 = C[:m]^T Y[:m] + out1."""
+        self._check(lib().rsdft_rotate_bf16x3(self._h, _ptr(y), y.shape[0], _ptr(c), c.shape[1],
+                                              _ptr(out0), _ptr(out1), _stream()))
 
     def rotate(self, y, c, out, base=None, sign=1):
         self._check(lib().rsdft_rotate(self._h, _ptr(y), y.shape[0], _ptr(c), c.shape[1], _ptr(base),

@@ -68,3 +68,69 @@ def test_mixed_lobpcg_with_tensor_core_grams_meets_fp64_bars():
     assert stats.converged and stats.iterations_mixed > 0
     assert np.max(np.abs(eig - o.eig)) < 1e-9
     assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
+
+
+def _rot_ref(y, c, m):
+    """FP64 reference of the split rotation on the same complex64 inputs."""
+    Y = y.astype(np.complex128)
+    out1 = c[m:].T @ Y[m:]
+    out0 = c[:m].T @ Y[:m] + out1
+    scale = np.abs(c).T @ np.abs(Y)          # sum_j |C_jb| |Y_j(r)| per output entry
+    return out0, out1, scale
+
+
+# Split-BF16 x3 error model for one output entry: each factor keeps ~2^-18 of
+# relative error after the hi/lo split, the dropped lo*lo' term is ~2^-18, and
+# the FP32 accumulation over k <= 432 terms adds at most ~k 2^-24; 5e-5 of
+# sum_j |C_jb||Y_j(r)| bounds the sum.
+ROT_TOL = 5e-5
+
+
+@pytest.mark.parametrize("N,k,m", [((24, 24, 24), 48, 16), ((20, 18, 15), 11, 5),
+                                   ((24, 24, 24), 432, 144), ((16, 16, 16), 300, 144),
+                                   ((20, 18, 15), 100, 33)])
+def test_rotate_bf16x3_matches_fp64(N, k, m):
+    ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
+    y = draw_x0(11, k, ctx.n).astype(np.complex64)
+    rng = np.random.default_rng(12)
+    c = (rng.standard_normal((k, m)) + 1j * rng.standard_normal((k, m))) / np.sqrt(k)
+    out0 = torch.full((m, ctx.n), complex(np.nan, np.nan), dtype=torch.complex64, device="cuda")
+    out1 = torch.full_like(out0, complex(np.nan, np.nan))
+    ctx.rotate_bf16x3(dev(y), dev(c), out0, out1)
+    r0, r1, scale = _rot_ref(y, c, m)
+    e0 = np.max(np.abs(host(out0) - r0) / scale)
+    e1 = np.max(np.abs(host(out1) - r1) / np.maximum(np.abs(c[m:]).T @ np.abs(y[m:]), 1e-30))
+    print(f"split-BF16 rotation k={k} m={m} n={ctx.n}: rel errors {e0:.2e} (X), {e1:.2e} (P)")
+    assert np.isfinite(host(out0)).all() and np.isfinite(host(out1)).all()
+    assert e0 < ROT_TOL and e1 < ROT_TOL
+
+
+def test_rotate_bf16x3_rejects_unsupported_shapes():
+    N = (12, 12, 12)
+    ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
+    y = torch.zeros((300, ctx.n), dtype=torch.complex64, device="cuda")
+    for k, m in [(256, 256), (300, 250)]:
+        c = torch.zeros((k, m), dtype=torch.complex128, device="cuda")
+        o = torch.zeros((m, ctx.n), dtype=torch.complex64, device="cuda")
+        with pytest.raises(R.RsdftError):
+            ctx.rotate_bf16x3(y[:k], c, o, o.clone())
+
+
+def test_mixed_lobpcg_with_tensor_core_rotations_meets_fp64_bars():
+    """tensor_cores = 2: Grams and Ritz rotations of the FP32 phase on tcgen05;
+    after the FP64 refinement the FP64 bars hold."""
+    from oracle.lobpcg import lobpcg as oracle_lobpcg
+    from tests.gpu_common import pair, subspace_distance
+    from workloads import diamond8_24
+    wl = diamond8_24()
+    ctx, ham, _ = pair(wl)
+    x0 = wl.x0(24)
+    x = dev(x0)
+    eig, res, stats, st = ctx.lobpcg(x, ctx.lobpcg_opts(maxit=200, tol=1e-9, precision=R.MIXED,
+                                                        tensor_cores=2))
+    o = oracle_lobpcg(ham, x0, maxit=200, tol=1e-9)
+    print(f"tensor-core (Gram + rotation) mixed LOBPCG: {stats.iterations_mixed} FP32 + "
+          f"{stats.iterations - stats.iterations_mixed} FP64 iterations")
+    assert stats.converged and stats.iterations_mixed > 0
+    assert np.max(np.abs(eig - o.eig)) < 1e-9
+    assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
