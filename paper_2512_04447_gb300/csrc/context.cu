@@ -66,11 +66,18 @@ static bool make_axis_plan(int N, AxisPlan &p) {
     p.N = N;
     p.nstage = (int)r.size();
     int len = N;
+    // ceil(2^32 / d): exact quotients for x < 2^16 and d < 2^16
+    auto mag = [](int d) -> unsigned {
+        return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
+    };
+    p.nmag = mag(N);
     for (int s = 0; s < p.nstage; ++s) {
         p.radix[s] = r[s];
         p.len[s] = len;
         p.sub[s] = len / r[s];
         len = p.sub[s];
+        p.submag[s] = mag(p.sub[s]);
+        p.bfmag[s] = mag(N / r[s]);
     }
     return true;
 }

@@ -24,17 +24,19 @@ __device__ __forceinline__ double2 c_mulc(double2 a, double2 b) {  // a * conj(b
 }
 __device__ __forceinline__ double2 c_conj(double2 a) { return make_double2(a.x, -a.y); }
 
-// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024).
+// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); the warp
+// partials are combined by warp 0 with shuffles (a chain of dependent FP64 adds
+// in one thread costs ~64 cycles per add on this part).
 __device__ double block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        sh[32] = s;
+    if (warp == 0) {
+        double s = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[32] = s;
     }
     __syncthreads();
     return sh[32];
@@ -91,10 +93,14 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
         }
         __syncthreads();
         if (!dr) {
+            // lower triangle of the trailing block, (i, c2) with c2 <= i, packed:
+            // t -> row offset ri with ri (ri + 1) / 2 <= t
             const int m = nb - (c + 1);
-            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-                const int i = c + 1 + t / m, c2 = c + 1 + t % m;
-                if (c2 > i) continue;
+            for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
+                int ri = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+                while (ri * (ri + 1) / 2 > t) --ri;
+                while ((ri + 1) * (ri + 2) / 2 <= t) ++ri;
+                const int i = c + 1 + ri, c2 = c + 1 + (t - ri * (ri + 1) / 2);
                 const double2 p = c_mulc(sD[i][c], sD[c2][c]);
                 sD[i][c2].x -= p.x;
                 sD[i][c2].y -= p.y;
@@ -328,7 +334,7 @@ static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc
                                int ldb, int ncol, cudaStream_t st) {
     for (int rb = 0; rb < kc; rb += NBK) {
         const int nb = std::min(NBK, kc - rb);
-        k_trsm_lower_diag<<<cdiv(ncol, 8), 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        k_trsm_lower_diag<<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
         count_launch(ctx);
         const int rest = kc - rb - nb;
         if (rest > 0) {
@@ -347,7 +353,7 @@ static rsdft_status trsm_upperH(rsdft_ctx *ctx, const double2 *L, int ldl, int k
     for (int q = nblk - 1; q >= 0; --q) {
         const int rb = q * NBK;
         const int nb = std::min(NBK, kc - rb);
-        k_trsm_upperH_diag<<<cdiv(ncol, 8), 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
+        k_trsm_upperH_diag<<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
         count_launch(ctx);
         if (rb > 0) {
             dim3 g(cdiv(ncol, 32), cdiv(rb, TRSM_TR));
@@ -520,13 +526,14 @@ __device__ double2 block_sum_c(double2 v, double2 *sh2) {
     __syncthreads();
     if (lane == 0) sh2[warp] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            s.x += sh2[w].x;
-            s.y += sh2[w].y;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        double2 s = lane < nw ? sh2[lane] : make_double2(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_down_sync(0xffffffffu, s.y, o);
         }
-        sh2[32] = s;
+        if (lane == 0) sh2[32] = s;
     }
     __syncthreads();
     return sh2[32];
@@ -670,14 +677,24 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
             double2 *row = a + (size_t)r * ld;
             const double2 vr = sv[r - o], wr = sw[r - o];
             double sx = 0.0, sy = 0.0;
+            // x = a - v_r conj(w_c) - w_r conj(v_c) and the matvec term x s_c as 12
+            // FMAs per element (an FP64 instruction costs the same whatever it fuses)
             for (int c = i + 2 + lane; c < k; c += 32) {
                 const double2 xv = ldcg2(row + c);
-                const double2 p = c_mulc(vr, sw[c - o]), q = c_mulc(wr, sv[c - o]);
-                const double2 x = make_double2(xv.x - p.x - q.x, xv.y - p.y - q.y);
-                row[c] = x;
-                const double2 m = c_mul(x, sn[c - i - 2]);
-                sx += m.x;
-                sy += m.y;
+                const double2 wc = sw[c - o], vc = sv[c - o], sc = sn[c - i - 2];
+                double xr = fma(-vr.x, wc.x, xv.x);
+                xr = fma(-vr.y, wc.y, xr);
+                xr = fma(-wr.x, vc.x, xr);
+                xr = fma(-wr.y, vc.y, xr);
+                double xi = fma(-vr.y, wc.x, xv.y);
+                xi = fma(vr.x, wc.y, xi);
+                xi = fma(-wr.y, vc.x, xi);
+                xi = fma(wr.x, vc.y, xi);
+                row[c] = make_double2(xr, xi);
+                sx = fma(xr, sc.x, sx);
+                sx = fma(-xi, sc.y, sx);
+                sy = fma(xr, sc.y, sy);
+                sy = fma(xi, sc.x, sy);
             }
             for (int o2 = 16; o2 > 0; o2 >>= 1) {
                 sx += __shfl_xor_sync(0xffffffffu, sx, o2);
@@ -731,14 +748,14 @@ __device__ int sturm_count(const double *__restrict__ d, const double *__restric
 // scr: [0] tnorm, [1] glo, [2] ghi, [3] pivmin, then e2[k]
 __device__ double block_reduce_max(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double r = sh[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
-        sh[32] = r;
+    if (warp == 0) {
+        double r = lane < nw ? sh[lane] : -1e300;
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+        if (lane == 0) sh[32] = r;
     }
     __syncthreads();
     return sh[32];

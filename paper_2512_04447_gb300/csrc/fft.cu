@@ -141,21 +141,27 @@ __device__ __forceinline__ void bfly(V *s, int base, int step, int j, int twstep
 // Element e of line l sits at s[l * lstride + e * es].  lines_fast selects the
 // thread mapping: consecutive threads take consecutive lines (use when es > 1
 // and lstride == 1), else consecutive butterflies of one line.
+// x / d for x < 2^16 from the multiply-high divisor of d (mag = 0 means d = 1).
+__device__ __forceinline__ int qdiv(int x, unsigned mag) { return mag ? (int)__umulhi((unsigned)x, mag) : x; }
+
+// nlmag: multiply-high divisor of nlines.  Quotients and remainders of the
+// index decomposition use it instead of integer division (total < 2^16).
 template <typename V, bool INV>
-__device__ void fft_lines(V *s, const AxisPlan &ax, const V *tw, int nlines, int lstride, int es,
-                          bool lines_fast) {
+__device__ void fft_lines(V *s, const AxisPlan &ax, const V *tw, int nlines, unsigned nlmag, int lstride,
+                          int es, bool lines_fast) {
     const int N = ax.N;
     for (int t = 0; t < ax.nstage; ++t) {
         const int st = INV ? ax.nstage - 1 - t : t;
         const int r = ax.radix[st], len = ax.len[st], sub = ax.sub[st];
+        const unsigned smag = ax.submag[st], bmag = ax.bfmag[st];
         const int nbf = N / r;
         const int total = nbf * nlines;
         const int twstep = N / len;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int line, bf;
-            if (lines_fast) { line = idx % nlines; bf = idx / nlines; }
-            else { bf = idx % nbf; line = idx / nbf; }
-            const int b = bf / sub, j = bf - b * sub;
+            if (lines_fast) { bf = qdiv(idx, nlmag); line = idx - bf * nlines; }
+            else { line = qdiv(idx, bmag); bf = idx - line * nbf; }
+            const int b = qdiv(bf, smag), j = bf - b * sub;
             const int base = line * lstride + (b * len + j) * es;
             const int step = sub * es;
             switch (r) {
@@ -234,8 +240,8 @@ k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = mk<V>((T)in[i], (T)0);
     }
     __syncthreads();
-    fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, Nx, 1, false);
-    fft_lines<V, false>(s_plane, tb.ax[1], tb.tw[1], Nx, 1, Nx, true);
+    fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, Nx, 1, false);
+    fft_lines<V, false>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, Nx, true);
     V *out = dst + band * n + off;
     for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) out[i] = s_plane[i];
 }
@@ -259,11 +265,11 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
     V *base = buf + band * n + (size_t)y * Nx;
     const int tot = Nx * Nz;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        int z = i / Nx, x = i - z * Nx;
+        const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
         s_slab[i] = base[z * zstride + x];
     }
     __syncthreads();
-    fft_lines<V, false>(s_slab, tb.ax[2], tb.tw[2], Nx, 1, Nx, true);
+    fft_lines<V, false>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
     const T inv_n = (T)(1.0 / (double)n);
     const T gy2 = tb.g2[1][y];
     T tk = (T)1;
@@ -273,7 +279,7 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
         tk = (T)t;
     }
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        int z = i / Nx, x = i - z * Nx;
+        const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
         T g2 = tb.g2[0][x] + gy2 + tb.g2[2][z];
         T f;
         if (MID == Mid::Kinetic) f = (T)0.5 * g2 * inv_n;
@@ -283,9 +289,9 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
         s_slab[i] = mk<V>(s_slab[i].x * f, s_slab[i].y * f);
     }
     __syncthreads();
-    fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, 1, Nx, true);
+    fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        int z = i / Nx, x = i - z * Nx;
+        const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
         base[z * zstride + x] = s_slab[i];
     }
 }
@@ -297,7 +303,7 @@ template <typename V, Epi EPI>
 __global__ void __launch_bounds__(FFT_THREADS)
 k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi,
              const typename Sc<V>::T *__restrict__ v, ProjT<typename Sc<V>::T> pt,
-             const V *__restrict__ p, V *__restrict__ out, double *__restrict__ rout) {
+             const V *__restrict__ p, V *__restrict__ out, double *__restrict__ rout, int stage_pe) {
     using T = typename Sc<V>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *s_plane = reinterpret_cast<V *>(smem_raw);
@@ -309,8 +315,8 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
     const V *in = buf + band * n + off;
     for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = in[i];
     __syncthreads();
-    fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, 1, Nx, true);
-    fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, Nx, 1, false);
+    fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, Nx, true);
+    fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, Nx, 1, false);
     if (EPI == Epi::Plain) {
         V *o = out + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = s_plane[i];
@@ -322,6 +328,17 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
         const T *vv = v + off;
         const int np = pt.natom * pt.nproj;
         const V *pb = p + (size_t)band * np;
+        // E_aj <beta_aj|psi> of this band, staged once per CTA after the plane
+        // (when it fits; else read from global memory)
+        V *s_pe = s_plane + plane;
+        if (stage_pe) {
+            for (int q = threadIdx.x; q < np; q += blockDim.x) {
+                const V c = pb[q];
+                const T e = pt.e_kb[q];
+                s_pe[q] = mk<V>(e * c.x, e * c.y);
+            }
+            __syncthreads();
+        }
         V *o = out + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
             V t = s_plane[i];
@@ -331,12 +348,18 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
             const int g = (int)off + i;
             const int e0 = pt.c_rowptr[g], e1 = pt.c_rowptr[g + 1];
             for (int e = e0; e < e1; ++e) {
-                const int a = pt.c_atom[e];
+                const int a0 = pt.c_atom[e] * pt.nproj;
                 const T *bt = pt.c_beta + 4 * (size_t)e;
                 for (int j = 0; j < pt.nproj; ++j) {
-                    const int aj = a * pt.nproj + j;
-                    const T c = bt[j] * pt.e_kb[aj];
-                    const V q = pb[aj];
+                    V q;
+                    if (stage_pe) {
+                        q = s_pe[a0 + j];
+                    } else {
+                        const V c = pb[a0 + j];
+                        const T ek = pt.e_kb[a0 + j];
+                        q = mk<V>(ek * c.x, ek * c.y);
+                    }
+                    const T c = bt[j];
                     ax += c * q.x;
                     ay += c * q.y;
                 }
@@ -418,6 +441,8 @@ template <typename V> static size_t plane_bytes(const rsdft_ctx *ctx) {
 template <typename V> static size_t slab_bytes(const rsdft_ctx *ctx) {
     return (size_t)ctx->N[0] * ctx->N[2] * sizeof(V);
 }
+
+constexpr size_t MAX_DYN_SMEM = 227 * 1024;   // largest dynamic shared memory of one CTA
 
 template <typename K> static rsdft_status set_smem(rsdft_ctx *ctx, K kernel, size_t bytes) {
     if (bytes > 48 * 1024)
@@ -503,13 +528,17 @@ rsdft_status fft_xy_inverse_t(rsdft_ctx *ctx, const V *buf, const V *psi, const 
     const auto *v = v_of(ctx, (V *)nullptr);
     if (rout) {
         RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Real>, sm));
-        k_xy_inverse<V, Epi::Real><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
+        k_xy_inverse<V, Epi::Real><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout, 0);
     } else if (psi) {
-        RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Hpsi>, sm));
-        k_xy_inverse<V, Epi::Hpsi><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
+        // the plane plus, when it fits, the band's E_aj <beta_aj|psi> after it
+        const size_t smh = sm + (size_t)pt.natom * pt.nproj * sizeof(V);
+        const int stage = smh <= MAX_DYN_SMEM ? 1 : 0;
+        const size_t smu = stage ? smh : sm;
+        RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Hpsi>, smu));
+        k_xy_inverse<V, Epi::Hpsi><<<grid, FFT_THREADS, smu, st>>>(tb, buf, psi, v, pt, p, out, rout, stage);
     } else {
         RS_TRY(set_smem(ctx, k_xy_inverse<V, Epi::Plain>, sm));
-        k_xy_inverse<V, Epi::Plain><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout);
+        k_xy_inverse<V, Epi::Plain><<<grid, FFT_THREADS, sm, st>>>(tb, buf, psi, v, pt, p, out, rout, 0);
     }
     RS_LAUNCHED(ctx, "k_xy_inverse");
     return RSDFT_OK;

@@ -194,7 +194,21 @@ __global__ void k_split_bf16(RowBlocksT<float2> src, int nrows, long long n, int
 __global__ void __launch_bounds__(THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
           const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M,
-          int N, int kb_total, int kb_per_split, float *__restrict__ part, int *err) {
+          int N, int kb_total, int kb_per_split, int tpb, int blk_rows, float *__restrict__ part, int *err) {
+    // tpb > 0: B is a stack of N / blk_rows blocks of blk_rows rows, each Hermitian
+    // against A; blockIdx.x = block * tpb + tile within the block, and tiles below
+    // the diagonal (tile < tm) are skipped (the reduction mirrors them).
+    int brow0, ncol0, nvalid;
+    if (tpb > 0) {
+        const int blk = blockIdx.x / tpb, tnb = blockIdx.x - blk * tpb;
+        if (tnb < (int)blockIdx.y) return;
+        brow0 = blk * blk_rows + tnb * BN;
+        ncol0 = brow0;
+        nvalid = blk_rows - tnb * BN;
+    } else {
+        brow0 = ncol0 = blockIdx.x * BN;
+        nvalid = N - ncol0;
+    }
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -203,7 +217,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
     __shared__ __align__(8) uint64_t acc_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    const int tn = blockIdx.x, tm = blockIdx.y, split = blockIdx.z;
+    const int tm = blockIdx.y, split = blockIdx.z;
     const int kb0 = split * kb_per_split;
     const int nkb = max(0, min(kb_total, kb0 + kb_per_split) - kb0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,8 +249,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
             const int kx = (kb0 + it) * BK;
             tma_load_2d(st, &mAh, &full_bar[s], kx, tm * BM);
             tma_load_2d(st + TILE_BYTES, &mAl, &full_bar[s], kx, tm * BM);
-            tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kx, tn * BN);
-            tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kx, tn * BN);
+            tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kx, brow0);
+            tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kx, brow0);
             issued = it + 1;
         }
         if (*abort) {
@@ -287,8 +301,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         if (write && row < M) {
-            float *dst = part + ((size_t)split * M + row) * N + (size_t)tn * BN + c0;
-            const int cmax = min(32, N - (tn * BN + c0));
+            float *dst = part + ((size_t)split * M + row) * N + (size_t)ncol0 + c0;
+            const int cmax = min(32, nvalid - c0);
 #pragma unroll
             for (int i = 0; i < 32; ++i)
                 if (i < cmax) dst[i] = v[i];
@@ -304,24 +318,45 @@ k_gram_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
 }
 
 // G_S and G_H of the LOBPCG basis from the split partials of
-// C = A [Y; Yrot; HY; HYrot]^T (N = 4k): Hermitised, scaled by dV, FP64 sums.
+// C = A [Y; Yrot; HY; HYrot]^T (N = 4k, upper 128-tiles of each block computed):
+// scaled by dV, FP64 sums; entries of tiles above the diagonal are taken as
+// computed, below it as the conjugate of the mirrored entry, and on diagonal
+// tiles the two are averaged (as the FP64 path does).
 __global__ void k_gram_tc_reduce_sh(const float *__restrict__ part, int splits, int k, double scale,
                                     double2 *__restrict__ gs, double2 *__restrict__ gh, int ld) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)k * k) return;
     const int i = (int)(idx / k), j = (int)(idx % k);
     const size_t N = 4 * (size_t)k, plane = (size_t)k * N;
-    double sr = 0, si = 0, hr = 0, hi = 0;
-    for (int s = 0; s < splits; ++s) {
-        const float *pi = part + s * plane + (size_t)i * N, *pj = part + s * plane + (size_t)j * N;
-        sr += (double)pi[j] + (double)pj[i];
-        si += (double)pi[k + j] - (double)pj[k + i];
-        hr += (double)pi[2 * k + j] + (double)pj[2 * k + i];
-        hi += (double)pi[3 * k + j] - (double)pj[3 * k + i];
+    auto sum4 = [&](int r, int c, double &sr, double &si, double &hr, double &hi) {
+        sr = si = hr = hi = 0.0;
+        for (int s = 0; s < splits; ++s) {
+            const float *pr = part + s * plane + (size_t)r * N;
+            sr += (double)pr[c];
+            si += (double)pr[k + c];
+            hr += (double)pr[2 * k + c];
+            hi += (double)pr[3 * k + c];
+        }
+    };
+    const int ti = i / BM, tj = j / BN;
+    double sr, si, hr, hi;
+    if (ti < tj) {
+        sum4(i, j, sr, si, hr, hi);
+    } else if (ti > tj) {
+        sum4(j, i, sr, si, hr, hi);
+        si = -si;
+        hi = -hi;
+    } else {
+        double sr2, si2, hr2, hi2;
+        sum4(i, j, sr, si, hr, hi);
+        sum4(j, i, sr2, si2, hr2, hi2);
+        sr = 0.5 * (sr + sr2);
+        si = 0.5 * (si - si2);
+        hr = 0.5 * (hr + hr2);
+        hi = 0.5 * (hi - hi2);
     }
-    const double h = 0.5 * scale;
-    gs[(size_t)i * ld + j] = make_double2(h * sr, h * si);
-    gh[(size_t)i * ld + j] = make_double2(h * hr, h * hi);
+    gs[(size_t)i * ld + j] = make_double2(scale * sr, scale * si);
+    gh[(size_t)i * ld + j] = make_double2(scale * hr, scale * hi);
 }
 
 // General G = A^H B from the partials of C = A [B; Brot]^T (N = 2 nb).
@@ -352,7 +387,8 @@ __global__ void k_gram_tc_reduce(const float *__restrict__ part, int splits, int
 // top and the sum is written as the new X (= X C_X + P).
 constexpr int RBK = 64;               // K rows (of Y) per pipeline stage
 constexpr int RSTAGES = 2;
-constexpr int RTHREADS = 192;         // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int RTHREADS = 320;         // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int REPI = 8;               // epilogue warps (two per TMEM lane quarter)
 constexpr int RA_CHUNK = 64 * RBK * 2;  // one 64-column chunk of A: 8 KB
 constexpr int MAX_NH = 240;
 
@@ -398,8 +434,8 @@ k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUten
          const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
          const __grid_constant__ CUtensorMap mBWPh, const __grid_constant__ CUtensorMap mBWPl,
          const __grid_constant__ CUtensorMap mBXh, const __grid_constant__ CUtensorMap mBXl, int nh,
-         int m, int kb_wp, int kb_x, long long two_n, int ntiles, float *__restrict__ out0,
-         float *__restrict__ out1, int *err) {
+         int m, int kb_wp, int kb_x, long long two_n, int ntiles, float *out0,
+         float *__restrict__ out1, const float *base, float sign, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -419,7 +455,7 @@ k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUten
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&accf_bar, 1);
-        mbar_init(&acce_bar, 4);
+        mbar_init(&acce_bar, REPI);
         mbar_init(&done_bar, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -474,10 +510,12 @@ k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUten
         int it = 0, ap = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            bool fresh = true;   // the tile's first MMA overwrites the accumulator
             for (int ph = 0; ph < 2 && !stop; ++ph) {
+                const int nkb = ph == 0 ? kb_wp : kb_x;
+                if (nkb == 0) continue;   // no [W P] rows: X phase only
                 if (ap > 0 && !mbar_wait(&acce_bar, (ap - 1) & 1, abort)) { stop = true; break; }
                 tc_fence_after();
-                const int nkb = ph == 0 ? kb_wp : kb_x;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % RSTAGES, r = it / RSTAGES;
                     if (!mbar_wait(&full_bar[s], r & 1, abort)) { stop = true; break; }
@@ -494,11 +532,12 @@ k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUten
                             const uint64_t bh = smem_desc(sb + half * bpart + kk * 32);
                             const uint64_t bl = smem_desc(sb + (2 + half) * bpart + kk * 32);
                             const uint32_t d = tmem + (uint32_t)(half * nh);
-                            const uint32_t acc = (ph == 0 && kb == 0 && kk == 0) ? 0u : 1u;
+                            const uint32_t acc = fresh ? 0u : 1u;
                             mma_bf16(d, ah, bh, idesc, acc);
                             mma_bf16(d, ah, bl, idesc, 1u);
                             mma_bf16(d, al, bh, idesc, 1u);
                         }
+                        fresh = false;
                     }
                     mma_commit(&empty_bar[s]);
                 }
@@ -514,25 +553,37 @@ k_rot_tc(const __grid_constant__ CUtensorMap mWPh, const __grid_constant__ CUten
             if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; break; }
         }
     } else if (warp >= 2) {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
-        const int q = warp & 3;
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; the two warps of
+        // a lane quarter take alternate 32-column chunks
+        const int q = warp & 3, half = (warp - 2) >> 2;
         int ap = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const long long m0 = (long long)t * 128;
             for (int ph = 0; ph < 2; ++ph) {
+                if ((ph == 0 ? kb_wp : kb_x) == 0) continue;
                 if (!mbar_wait(&accf_bar, ap & 1, abort)) break;
                 tc_fence_after();
                 float *out = ph == 0 ? out1 : out0;
+                const float *bse = ph == 0 ? nullptr : base;
                 const long long p = m0 + q * 32 + lane;
-                for (int b0 = 0; b0 < m; b0 += 32) {
-                    float vr[32], vi[32];
+                for (int b0 = half * 32; b0 < m; b0 += 64) {
+                    float vr[32], vi[32], bv[32];
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b0, vr);
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(nh + b0), vi);
+                    if (bse) {
+                        // all base loads of the chunk before any store (out may alias base)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            bv[i] = (b0 + i < m && p < two_n) ? bse[(size_t)(b0 + i) * two_n + p] : 0.0f;
+                    }
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const float pv = __shfl_xor_sync(0xffffffffu, vi[i], 1);
                         const float v = (lane & 1) ? vr[i] + pv : vr[i] - pv;
-                        if (out && b0 + i < m && p < two_n) out[(size_t)(b0 + i) * two_n + p] = v;
+                        if (out && b0 + i < m && p < two_n) {
+                            const size_t o = (size_t)(b0 + i) * two_n + p;
+                            out[o] = bse ? bv[i] + sign * v : v;
+                        }
                     }
                 }
                 tc_fence_before();
@@ -651,8 +702,11 @@ static rsdft_status split_rows(rsdft_ctx *ctx, const RowBlocksT<float2> &src, in
     return RSDFT_OK;
 }
 
-// C = A B^T over K = 2n for A rows [0, M), B rows [0, N) already split; returns splits.
-static rsdft_status gemm(rsdft_ctx *ctx, const Buffers &b, int M, int N, cudaStream_t st, int *splits_out) {
+// C = A B^T over K = 2n for A rows [0, M), B rows [0, N) already split; returns
+// splits.  blk_rows > 0: B is N / blk_rows blocks Hermitian against A (upper
+// tiles of each block only).
+static rsdft_status gemm(rsdft_ctx *ctx, const Buffers &b, int M, int N, cudaStream_t st, int *splits_out,
+                         int blk_rows = 0) {
     RS_TRY(encoder(ctx));
     const long long K = 2 * ctx->n;
     CUtensorMap mAh, mAl, mBh, mBl;
@@ -660,14 +714,18 @@ static rsdft_status gemm(rsdft_ctx *ctx, const Buffers &b, int M, int N, cudaStr
     RS_TRY(make_map(ctx, &mAl, b.al, K, M, b.ldk));
     RS_TRY(make_map(ctx, &mBh, b.bh, K, N, b.ldk));
     RS_TRY(make_map(ctx, &mBl, b.bl, K, N, b.ldk));
-    const int tn = cdiv(N, BN), tm = cdiv(M, BM);
+    const int tm = cdiv(M, BM);
+    const int tpb = blk_rows > 0 ? cdiv(blk_rows, BN) : 0;
+    const int tn = blk_rows > 0 ? (N / blk_rows) * tpb : cdiv(N, BN);
+    // tiles that do work: all, or the upper ones of each Hermitian block
+    const long long active = blk_rows > 0 ? (long long)(N / blk_rows) * tpb * (tpb + 1) / 2 : (long long)tn * tm;
     const int kb_total = (int)((K + BK - 1) / BK);
     // splits: whole waves of one CTA per SM, at least 8 k-blocks per CTA
     int splits = 1;
     double best = 0.0;
     for (int s = 1; s <= 256 && s <= kb_total; ++s) {
         if (s > 1 && kb_total / s < 8) break;
-        const long long ctas = (long long)tn * tm * s;
+        const long long ctas = active * s;
         const long long waves = (ctas + ctx->num_sms - 1) / ctx->num_sms;
         const double eff = (double)ctas / (double)(waves * ctx->num_sms);
         if (eff > best + 1e-9) { best = eff; splits = s; }
@@ -683,10 +741,12 @@ static rsdft_status gemm(rsdft_ctx *ctx, const Buffers &b, int M, int N, cudaStr
         attr = true;
     }
     {
-        ProfScope ps(ctx, RSDFT_K_GRAM_TC, 3.0 * 2.0 * (double)M * N * K,
+        const double frac = blk_rows > 0 ? (double)active / ((double)tn * tm) : 1.0;
+        ProfScope ps(ctx, RSDFT_K_GRAM_TC, 3.0 * 2.0 * (double)M * N * K * frac,
                      4.0 * (double)K * (M + N), st);
         k_gram_tc<<<dim3(tn, tm, splits), THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kb_total,
-                                                                     kbs, ctx->ws.tcpart, ctx->ws.tcerr);
+                                                                     kbs, tpb, blk_rows, ctx->ws.tcpart,
+                                                                     ctx->ws.tcerr);
     }
     RS_LAUNCHED(ctx, "k_gram_tc");
     *splits_out = splits;
@@ -707,11 +767,25 @@ struct RotCoef {
     int kpad_wp, kpad_x;
 };
 
-static rsdft_status rot_coef(rsdft_ctx *ctx, const double2 *c, int ldc, int k, int m, int nh, RotCoef &rc,
-                             cudaStream_t st) {
+// One rotation out0 = base + sign (X C_X + WP C_WP), out1 = WP C_WP (when kwp > 0):
+// X = kx split rows at (xh, xl), WP = kwp split rows at (wph, wpl), leading
+// dimension ldk; C rows [0, kx) multiply X, rows [kx, kx + kwp) multiply WP;
+// ncol output bands.
+struct RotSpec {
+    const __nv_bfloat16 *xh, *xl, *wph, *wpl;
+    long long ldk;
+    int kx, kwp;
+    const double2 *c;
+    int ldc, ncol;
+    float2 *out0, *out1;
+    const float2 *base;
+    int sign;
+};
+
+static rsdft_status rot_coef(rsdft_ctx *ctx, const RotSpec &sp, int nh, RotCoef &rc, cudaStream_t st) {
     Workspace &w = ctx->ws;
-    rc.kpad_wp = cdiv(k - m, RBK) * RBK;
-    rc.kpad_x = cdiv(m, RBK) * RBK;
+    rc.kpad_wp = cdiv(sp.kwp, RBK) * RBK;
+    rc.kpad_x = cdiv(sp.kx, RBK) * RBK;
     const size_t per_wp = (size_t)2 * nh * rc.kpad_wp, per_x = (size_t)2 * nh * rc.kpad_x;
     const size_t need = 2 * (per_wp + per_x) * sizeof(__nv_bfloat16) + 256;
     if (need > w.tcrot_bytes) {
@@ -729,31 +803,40 @@ static rsdft_status rot_coef(rsdft_ctx *ctx, const double2 *c, int ldc, int k, i
     rc.wpl = rc.wph + per_wp;
     rc.xh = rc.wpl + per_wp;
     rc.xl = rc.xh + per_x;
-    k_rot_coef<<<cdiv((long long)per_wp, 256), 256, 0, st>>>(c, ldc, m, k - m, m, nh, rc.kpad_wp, rc.wph, rc.wpl);
-    k_rot_coef<<<cdiv((long long)per_x, 256), 256, 0, st>>>(c, ldc, 0, m, m, nh, rc.kpad_x, rc.xh, rc.xl);
-    count_launch(ctx, 2);
+    if (per_wp > 0) {
+        k_rot_coef<<<cdiv((long long)per_wp, 256), 256, 0, st>>>(sp.c, sp.ldc, sp.kx, sp.kwp, sp.ncol, nh,
+                                                                  rc.kpad_wp, rc.wph, rc.wpl);
+        count_launch(ctx);
+    }
+    k_rot_coef<<<cdiv((long long)per_x, 256), 256, 0, st>>>(sp.c, sp.ldc, 0, sp.kx, sp.ncol, nh, rc.kpad_x,
+                                                             rc.xh, rc.xl);
+    count_launch(ctx);
     RS_LAUNCHED(ctx, "k_rot_coef");
     return RSDFT_OK;
 }
 
-// out0 = Y C, out1 = Y[m:k] C[m:k] with Y the split rows row0 .. row0 + k of b.
-static rsdft_status rotate_launch(rsdft_ctx *ctx, const Buffers &b, int row0, int k, const double2 *c, int ldc,
-                                  int m, float2 *out0, float2 *out1, cudaStream_t st) {
+static rsdft_status rotate_launch(rsdft_ctx *ctx, const RotSpec &sp, cudaStream_t st) {
     RS_TRY(encoder(ctx));
-    const int nh = cdiv(m, 16) * 16;
+    const int nh = cdiv(sp.ncol, 16) * 16;
     RotCoef rc;
-    RS_TRY(rot_coef(ctx, c, ldc, k, m, nh, rc, st));
+    RS_TRY(rot_coef(ctx, sp, nh, rc, st));
     const long long two_n = 2 * ctx->n;
     CUtensorMap mWPh, mWPl, mXh, mXl, mBWPh, mBWPl, mBXh, mBXl;
-    const size_t off_wp = (size_t)(row0 + m) * b.ldk, off_x = (size_t)row0 * b.ldk;
-    RS_TRY(make_map(ctx, &mWPh, b.bh + off_wp, two_n, k - m, b.ldk, RBK));
-    RS_TRY(make_map(ctx, &mWPl, b.bl + off_wp, two_n, k - m, b.ldk, RBK));
-    RS_TRY(make_map(ctx, &mXh, b.bh + off_x, two_n, m, b.ldk, RBK));
-    RS_TRY(make_map(ctx, &mXl, b.bl + off_x, two_n, m, b.ldk, RBK));
-    RS_TRY(make_map(ctx, &mBWPh, rc.wph, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
-    RS_TRY(make_map(ctx, &mBWPl, rc.wpl, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
+    RS_TRY(make_map(ctx, &mXh, sp.xh, two_n, sp.kx, sp.ldk, RBK));
+    RS_TRY(make_map(ctx, &mXl, sp.xl, two_n, sp.kx, sp.ldk, RBK));
     RS_TRY(make_map(ctx, &mBXh, rc.xh, rc.kpad_x, 2 * nh, rc.kpad_x, nh));
     RS_TRY(make_map(ctx, &mBXl, rc.xl, rc.kpad_x, 2 * nh, rc.kpad_x, nh));
+    if (sp.kwp > 0) {
+        RS_TRY(make_map(ctx, &mWPh, sp.wph, two_n, sp.kwp, sp.ldk, RBK));
+        RS_TRY(make_map(ctx, &mWPl, sp.wpl, two_n, sp.kwp, sp.ldk, RBK));
+        RS_TRY(make_map(ctx, &mBWPh, rc.wph, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
+        RS_TRY(make_map(ctx, &mBWPl, rc.wpl, rc.kpad_wp, 2 * nh, rc.kpad_wp, nh));
+    } else {
+        mWPh = mXh;   // never read: the [W P] phase has no k-blocks
+        mWPl = mXl;
+        mBWPh = mBXh;
+        mBWPl = mBXl;
+    }
     RS_TRY(partials(ctx, 0));
     RS_CUDA(ctx, cudaMemsetAsync(ctx->ws.tcerr, 0, sizeof(int), st));
     const int smem = RSTAGES * rot_stage_bytes(nh) + 1024;
@@ -764,17 +847,43 @@ static rsdft_status rotate_launch(rsdft_ctx *ctx, const Buffers &b, int row0, in
     }
     const int ntiles = (int)((two_n + 127) / 128);
     const int grid = std::min(ntiles, ctx->num_sms);
+    const int k = sp.kx + sp.kwp;
     {
-        ProfScope ps(ctx, RSDFT_K_ROTATE_TC, 3.0 * 2.0 * (double)two_n * (2.0 * m) * k,
-                     2.0 * 2.0 * (double)k * two_n + 2.0 * 4.0 * (double)m * two_n, st);
-        k_rot_tc<<<grid, RTHREADS, smem, st>>>(mWPh, mWPl, mXh, mXl, mBWPh, mBWPl, mBXh, mBXl, nh, m,
+        ProfScope ps(ctx, RSDFT_K_ROTATE_TC, 3.0 * 2.0 * (double)two_n * (2.0 * sp.ncol) * k,
+                     2.0 * 2.0 * (double)k * two_n +
+                         4.0 * (double)sp.ncol * two_n * ((sp.out1 ? 2.0 : 1.0) + (sp.base ? 1.0 : 0.0)),
+                     st);
+        k_rot_tc<<<grid, RTHREADS, smem, st>>>(mWPh, mWPl, mXh, mXl, mBWPh, mBWPl, mBXh, mBXl, nh, sp.ncol,
                                                 rc.kpad_wp / RBK, rc.kpad_x / RBK, two_n, ntiles,
-                                                reinterpret_cast<float *>(out0),
-                                                reinterpret_cast<float *>(out1), ctx->ws.tcerr);
+                                                reinterpret_cast<float *>(sp.out0),
+                                                reinterpret_cast<float *>(sp.out1),
+                                                reinterpret_cast<const float *>(sp.base), (float)sp.sign,
+                                                ctx->ws.tcerr);
     }
     count_launch(ctx);
     RS_LAUNCHED(ctx, "k_rot_tc");
     return check_err(ctx, st);
+}
+
+// Ritz rotation of split rows row0 .. row0 + k of b (X = the first m rows).
+static rsdft_status rotate_rows(rsdft_ctx *ctx, const Buffers &b, int row0, int k, const double2 *c, int ldc,
+                                int m, float2 *out0, float2 *out1, cudaStream_t st) {
+    RotSpec sp;
+    sp.xh = b.bh + (size_t)row0 * b.ldk;
+    sp.xl = b.bl + (size_t)row0 * b.ldk;
+    sp.wph = b.bh + (size_t)(row0 + m) * b.ldk;
+    sp.wpl = b.bl + (size_t)(row0 + m) * b.ldk;
+    sp.ldk = b.ldk;
+    sp.kx = m;
+    sp.kwp = k - m;
+    sp.c = c;
+    sp.ldc = ldc;
+    sp.ncol = m;
+    sp.out0 = out0;
+    sp.out1 = out1;
+    sp.base = nullptr;
+    sp.sign = 1;
+    return rotate_launch(ctx, sp, st);
 }
 
 }  // namespace tc
@@ -796,7 +905,7 @@ rsdft_status gram_tc_sh(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const RowBl
     RS_TRY(tc::split_rows(ctx, HY, 0, b.bh, b.bl, 2 * k, b.ldk, st));
     RS_TRY(tc::split_rows(ctx, HY, 1, b.bh, b.bl, 3 * k, b.ldk, st));
     int splits = 0;
-    RS_TRY(tc::gemm(ctx, b, k, 4 * k, st, &splits));
+    RS_TRY(tc::gemm(ctx, b, k, 4 * k, st, &splits, k));
     tc::k_gram_tc_reduce_sh<<<cdiv((long long)k * k, 256), 256, 0, st>>>(ctx->ws.tcpart, splits, k, ctx->dV,
                                                                           gs, gh, ld);
     count_launch(ctx);
@@ -823,6 +932,30 @@ rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlock
     return tc::check_err(ctx, st);
 }
 
+// W <- W - X C (C = <X|W>, m x na, ld na) on the tensor cores, from the X split
+// rows that the preceding gram_tc(X, W) left in the A region of the workspace.
+rsdft_status rotate_tc_ortho(rsdft_ctx *ctx, int m, int na, const double2 *c, float2 *w, cudaStream_t st) {
+    if (m < 1 || na < 1 || cdiv(na, 16) * 16 > tc::MAX_NH)
+        return fail(ctx, RSDFT_E_INVALID, "tensor-core orthogonalisation: m %d, na %d", m, na);
+    tc::Buffers b;
+    RS_TRY(tc::buffers(ctx, m, 2 * na, b));   // the layout gram_tc(X, W) wrote
+    tc::RotSpec sp;
+    sp.xh = b.ah;
+    sp.xl = b.al;
+    sp.wph = sp.wpl = nullptr;
+    sp.ldk = b.ldk;
+    sp.kx = m;
+    sp.kwp = 0;
+    sp.c = c;
+    sp.ldc = na;
+    sp.ncol = na;
+    sp.out0 = w;
+    sp.out1 = nullptr;
+    sp.base = w;
+    sp.sign = -1;
+    return tc::rotate_launch(ctx, sp, st);
+}
+
 bool rotate_tc_fits(int k, int m) { return m >= 1 && k > m && cdiv(m, 16) * 16 <= tc::MAX_NH; }
 
 rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
@@ -830,7 +963,7 @@ rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c,
     if (!rotate_tc_fits(k, m)) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
     tc::Buffers b;
     RS_TRY(tc::buffers(ctx, 0, 4 * k, b));   // the layout gram_tc_sh wrote
-    return tc::rotate_launch(ctx, b, which == 0 ? 0 : 2 * k, k, c, ldc, m, out0, out1, st);
+    return tc::rotate_rows(ctx, b, which == 0 ? 0 : 2 * k, k, c, ldc, m, out0, out1, st);
 }
 
 rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c, int ldc, int m,
@@ -840,7 +973,7 @@ rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c,
     RS_TRY(tc::buffers(ctx, 0, k, b));
     RowBlocksT<float2> Y{{y, nullptr, nullptr}, {k, 0, 0}};
     RS_TRY(tc::split_rows(ctx, Y, 0, b.bh, b.bl, 0, b.ldk, st));
-    return tc::rotate_launch(ctx, b, 0, k, c, ldc, m, out0, out1, st);
+    return tc::rotate_rows(ctx, b, 0, k, c, ldc, m, out0, out1, st);
 }
 
 }  // namespace rsdft

@@ -35,14 +35,14 @@ constexpr double P_DROP_FP32 = 1e-4;
 
 __device__ __forceinline__ double block_sum2(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        sh[32] = s;
+    if (warp == 0) {
+        double s = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[32] = s;
     }
     __syncthreads();
     return sh[32];
@@ -473,13 +473,19 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         {
             Blocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
             Blocks YW{{W, nullptr, nullptr}, {na, 0, 0}};
+            bool done = false;
             if constexpr (std::is_same<V, float2>::value) {
                 if (tc) RS_TRY(gram_tc(ctx, YX, YW, w.C, na, st));
                 else RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
+                if (tc_rot && rotate_tc_fits(m + na, na)) {
+                    // the X split rows of the Gram above are still in the workspace
+                    RS_TRY(rotate_tc_ortho(ctx, m, na, w.C, W, st));
+                    done = true;
+                }
             } else {
                 RS_TRY(Ops<V>::gram(ctx, YX, YW, w.C, na, false, dV, st));
             }
-            RS_TRY(Ops<V>::rotate(ctx, YX, w.C, na, na, W, -1, W, nullptr, st));
+            if (!done) RS_TRY(Ops<V>::rotate(ctx, YX, w.C, na, na, W, -1, W, nullptr, st));
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[1], st));
         RS_TRY(Ops<V>::apply_h(ctx, W, HW, na, st));

@@ -25,6 +25,10 @@ struct AxisPlan {
     int radix[MAX_STAGES];
     int len[MAX_STAGES];
     int sub[MAX_STAGES];
+    // multiply-high divisors: x / d == __umulhi(x, mag) for x < 2^16 (mag = 0 for d = 1)
+    unsigned nmag;                  // d = N
+    unsigned submag[MAX_STAGES];    // d = sub[s]
+    unsigned bfmag[MAX_STAGES];     // d = N / radix[s]
 };
 
 struct Fft3Plan {
@@ -232,6 +236,9 @@ rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlock
 bool rotate_tc_fits(int k, int m);
 rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
                              float2 *out0, float2 *out1, cudaStream_t st);
+// W <- W - X C (C = <X|W>, m x na) from the X split rows that the preceding
+// gram_tc(X, W) left in the workspace.
+rsdft_status rotate_tc_ortho(rsdft_ctx *ctx, int m, int na, const double2 *c, float2 *w, cudaStream_t st);
 // Same for an arbitrary FP32 block y [k][n] (splits it first).
 rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c, int ldc, int m,
                        float2 *out0, float2 *out1, cudaStream_t st);
