@@ -988,6 +988,72 @@ __global__ void k_backtransform(int k, const double2 *__restrict__ vh, int ldv,
     for (int r = threadIdx.x; r < k; r += blockDim.x) z[(size_t)r * ldz + j] = sz[r];
 }
 
+// Same, with row r of the vector held in registers by thread r % blockDim.x
+// (R rows per thread, k <= R blockDim.x): no barrier between reflectors besides
+// the one complex reduction, and the next reflector's elements are loaded
+// while the current one is applied.
+constexpr int BT_R = 4;
+__global__ void __launch_bounds__(1024)
+k_backtransform_reg(int k, const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tau,
+                    const double *__restrict__ zt, double2 *z, int ldz) {
+    __shared__ double2 sh2[33];
+    const int j = blockIdx.x, t = threadIdx.x, bd = blockDim.x;
+    double2 zr[BT_R], vc[BT_R], vn[BT_R];
+#pragma unroll
+    for (int q = 0; q < BT_R; ++q) {
+        const int r = t + q * bd;
+        zr[q] = make_double2(r < k ? zt[(size_t)j * k + r] : 0.0, 0.0);
+    }
+    int i = k - 2;
+    double2 tc = make_double2(0.0, 0.0);
+    if (i >= 0) {
+        tc = tau[i];
+#pragma unroll
+        for (int q = 0; q < BT_R; ++q) {
+            const int r = t + q * bd;
+            vc[q] = (r > i && r < k) ? vh[(size_t)i * ldv + r] : make_double2(0.0, 0.0);
+        }
+    }
+    for (; i >= 0; --i) {
+        double2 tn = make_double2(0.0, 0.0);
+        if (i > 0) {
+            tn = tau[i - 1];
+#pragma unroll
+            for (int q = 0; q < BT_R; ++q) {
+                const int r = t + q * bd;
+                vn[q] = (r > i - 1 && r < k) ? vh[(size_t)(i - 1) * ldv + r] : make_double2(0.0, 0.0);
+            }
+        }
+        if (tc.x != 0.0 || tc.y != 0.0) {   // uniform over the block
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < BT_R; ++q) {   // conj(v) z
+                acc.x = fma(vc[q].x, zr[q].x, acc.x);
+                acc.x = fma(vc[q].y, zr[q].y, acc.x);
+                acc.y = fma(vc[q].x, zr[q].y, acc.y);
+                acc.y = fma(-vc[q].y, zr[q].x, acc.y);
+            }
+            acc = block_sum_c(acc, sh2);
+            const double2 f = c_mul(tc, acc);
+#pragma unroll
+            for (int q = 0; q < BT_R; ++q) {   // z -= f v
+                zr[q].x = fma(-f.x, vc[q].x, zr[q].x);
+                zr[q].x = fma(f.y, vc[q].y, zr[q].x);
+                zr[q].y = fma(-f.x, vc[q].y, zr[q].y);
+                zr[q].y = fma(-f.y, vc[q].x, zr[q].y);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BT_R; ++q) vc[q] = vn[q];
+        tc = tn;
+    }
+#pragma unroll
+    for (int q = 0; q < BT_R; ++q) {
+        const int r = t + q * bd;
+        if (r < k) z[(size_t)r * ldz + j] = zr[q];
+    }
+}
+
 rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
                          double2 *z, int ldz, cudaStream_t st) {
     Workspace &w = ctx->ws;
@@ -1076,7 +1142,13 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     count_launch(ctx);
     k_cluster_gs<<<nkeep, 256, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
     count_launch(ctx);
-    k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
+    {
+        const int bt_threads = std::max(32, cdiv(cdiv(k, BT_R), 32) * 32);
+        if (bt_threads <= 1024)
+            k_backtransform_reg<<<nkeep, bt_threads, 0, st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
+        else
+            k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
+    }
     count_launch(ctx);
     RS_LAUNCHED(ctx, "tridiagonal eigensolve");
     if (coop_done) {

@@ -184,6 +184,7 @@ template <typename V> struct FftTabs {
     AxisPlan ax[3];
     const V *tw[3];
     const typename Sc<V>::T *g2[3];
+    double inv_n;   // 1 / (Nx Ny Nz), formed on the host
 };
 
 static FftTabs<double2> tabs_of(const rsdft_ctx *ctx, double2 *) {
@@ -193,6 +194,7 @@ static FftTabs<double2> tabs_of(const rsdft_ctx *ctx, double2 *) {
         t.tw[a] = ctx->fft.tw64[a];
         t.g2[a] = ctx->fft.g2pos[a];
     }
+    t.inv_n = 1.0 / (double)ctx->n;
     return t;
 }
 static FftTabs<float2> tabs_of(const rsdft_ctx *ctx, float2 *) {
@@ -202,6 +204,7 @@ static FftTabs<float2> tabs_of(const rsdft_ctx *ctx, float2 *) {
         t.tw[a] = ctx->fft.tw32[a];
         t.g2[a] = ctx->fft.g2pos32[a];
     }
+    t.inv_n = 1.0 / (double)ctx->n;
     return t;
 }
 static const ProjT<double> &proj_of(const rsdft_ctx *ctx, double2 *) { return ctx->pt; }
@@ -270,7 +273,7 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
     }
     __syncthreads();
     fft_lines<V, false>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
-    const T inv_n = (T)(1.0 / (double)n);
+    const T inv_n = (T)tb.inv_n;
     const T gy2 = tb.g2[1][y];
     T tk = (T)1;
     if (MID == Mid::Tpa) {

@@ -960,7 +960,9 @@ bool rotate_tc_fits(int k, int m) { return m >= 1 && k > m && cdiv(m, 16) * 16 <
 
 rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
                              float2 *out0, float2 *out1, cudaStream_t st) {
-    if (!rotate_tc_fits(k, m)) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
+    // k == m (X only, no new P) is allowed when out1 is NULL
+    const bool ok = rotate_tc_fits(k, m) || (k == m && !out1 && m >= 1 && cdiv(m, 16) * 16 <= tc::MAX_NH);
+    if (!ok) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
     tc::Buffers b;
     RS_TRY(tc::buffers(ctx, 0, 4 * k, b));   // the layout gram_tc_sh wrote
     return tc::rotate_rows(ctx, b, which == 0 ? 0 : 2 * k, k, c, ldc, m, out0, out1, st);

@@ -212,7 +212,11 @@ template <typename V>
 __global__ void k_scale_rows(V *a, V *a2, long long n, const double *__restrict__ nrm) {
     using T = decltype(V{}.x);
     const int b = blockIdx.y;
-    const T s = (T)(1.0 / nrm[b]);
+    // one reciprocal per thread: FP32 for FP32 rows (an FP64 division costs
+    // ~640 cycles per warp here), FP64 for FP64 rows
+    T s;
+    if constexpr (std::is_same<T, float>::value) s = 1.0f / (float)nrm[b];
+    else s = 1.0 / nrm[b];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         V &x = a[(size_t)b * n + i];
@@ -409,8 +413,18 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         RS_TRY(gram_pair(ctx, Y, HY, w.GS, w.GH, m, tc, st));
         int nd = 0;
         RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, pivot_tol, w.theta, w.Cfull, &nd, st));
-        RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
-        RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
+        bool rotated = false;
+        if constexpr (std::is_same<V, float2>::value) {
+            if (tc_rot && rotate_tc_fits(m + 1, m)) {   // X-only rotation from the Gram's split rows
+                RS_TRY(rotate_tc_split(ctx, 0, m, w.Cfull, m, m, Xn, nullptr, st));
+                RS_TRY(rotate_tc_split(ctx, 1, m, w.Cfull, m, m, HXn, nullptr, st));
+                rotated = true;
+            }
+        }
+        if (!rotated) {
+            RS_TRY(Ops<V>::rotate(ctx, Y, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
+            RS_TRY(Ops<V>::rotate(ctx, HY, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
+        }
         std::swap(X, Xn);
         std::swap(HX, HXn);
     }
@@ -458,6 +472,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[0], st));
         // ---- preconditioned residuals W (compact over the active bands)
         const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
+        const dim3 scalegrid(std::max(1, std::min(cdiv(n, 256 * 8), 256)), na);   // >= 8 points per thread
         if (o.precond == RSDFT_PRECOND_TPA) {
             RS_TRY(Ops<V>::project(ctx, X, proj, m, st));
             k_tkin<V><<<cdiv(na, 128), 128, 0, st>>>(w.theta, w.vexp, proj, ctx->pt, w.act, na, w.tkin);
@@ -491,14 +506,14 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         RS_TRY(Ops<V>::apply_h(ctx, W, HW, na, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[2], st));
         RS_TRY(row_norms<V>(ctx, W, na, w.nrm, st));
-        k_scale_rows<V><<<rowgrid, 256, 0, st>>>(W, HW, n, w.nrm);
+        k_scale_rows<V><<<scalegrid, 256, 0, st>>>(W, HW, n, w.nrm);
         count_launch(ctx);
         RS_LAUNCHED(ctx, "normalise W");
         if (np_ > 0) {
             const dim3 pgrid(rowgrid.x, np_);
             k_gather_rows<V><<<pgrid, 256, 0, st>>>(P, HP, actp, n, Pn, HPn);
             RS_TRY(row_norms<V>(ctx, Pn, np_, w.nrm, st));
-            k_scale_rows<V><<<pgrid, 256, 0, st>>>(Pn, HPn, n, w.nrm);
+            k_scale_rows<V><<<dim3(scalegrid.x, np_), 256, 0, st>>>(Pn, HPn, n, w.nrm);
             count_launch(ctx, 2);
             RS_LAUNCHED(ctx, "normalise P");
         }
