@@ -239,6 +239,10 @@ typedef struct {
     int iterations_mixed;  /* of which in the FP32 data path (RSDFT_MIXED)         */
     int converged;         /* 1 if the tolerance test passed                       */
     int dropped;           /* basis columns dropped by the Cholesky, summed        */
+    int coop_fallbacks;    /* subspace tridiagonalisations that ran as one launch
+                              per Householder step because the cooperative launch
+                              was refused (same result up to rounding)           */
+    int coop_last_error;   /* cudaError_t of the last refused cooperative launch   */
     double ms_hpsi, ms_precond, ms_gram, ms_dense, ms_rotate, ms_other;
 } rsdft_lobpcg_stats;
 
@@ -247,6 +251,29 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *opts);
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
                           double *eig_host, double *resnorm_host, rsdft_lobpcg_stats *stats,
                           void *stream);
+
+/* Batched LOBPCG (the batched form of the solve: many independent cells of
+ * uneven grid and band counts on one GPU).  ncell cells, each with its own
+ * context ctxs[c] and orbital block x_dev[c] ([nband[c]][n_c] complex128,
+ * device, in/out), solved with options opts[c] (one entry per cell, e.g. a
+ * different nconv per cell; NULL = defaults for all).  Up to max_concurrent cells
+ * (<= 0: min(ncell, 8)) are in flight at a time, each on its own stream driven
+ * by its own host thread, so that one cell's latency-bound subspace eigensolve
+ * overlaps the FFT and GEMM work of the others; the cooperative
+ * tridiagonalisations of different cells never run at the same time.  The call
+ * first waits for all work already issued on the device (the cells' streams do
+ * not order against the caller's streams) and returns after every cell's work
+ * has completed.  Per cell
+ * the results equal those of rsdft_lobpcg with the same options (same kernels,
+ * same launch shapes).  eig_host[c], res_host[c]: [nband[c]] host outputs (the
+ * arrays may be NULL); stats: ncell entries or NULL.  Returns the first failing
+ * cell's status and its index in *failed_cell (-1 when all succeed; may be
+ * NULL); the other cells still complete.  Contexts must not be shared between
+ * cells or used by other threads during the call. */
+rsdft_status rsdft_lobpcg_batched(rsdft_ctx *const *ctxs, int ncell, void *const *x_dev, const int *nband,
+                                  const rsdft_lobpcg_opts *opts /* [ncell] */, double *const *eig_host,
+                                  double *const *res_host, rsdft_lobpcg_stats *stats, int max_concurrent,
+                                  int *failed_cell);
 
 /* ---------------------------------------------------------------------------
  * SCF step: V_eff = V_loc + V_H[rho_in] + v_xc[rho_in] (FFT Hartree, LDA
@@ -334,6 +361,16 @@ rsdft_status rsdft_profile_read(rsdft_ctx *ctx, int kernel_id, double *ms, long 
                                 double *flops, double *bytes);
 /* Kernels launched on ctx since creation (every kernel, profiled or not). */
 long long rsdft_launch_count(const rsdft_ctx *ctx);
+
+/* Autotuner (off by default).  When on, the first call of each shape of the
+ * Gram GEMMs (tile edge 16 P, P = 2, 3, 4), the Ritz rotations (band tile
+ * 16 PB, PB = 1..4; not the in-place W update) and the tensor-core Gram (split
+ * count: the wave rule's, half, double) runs every candidate once, timed with
+ * CUDA events on the call's stream (the call synchronises), and later calls of
+ * that shape on this context use the fastest.  Candidates differ only in the
+ * summation order, so results agree to rounding.  on = 0 switches it off and
+ * forgets the choices. */
+rsdft_status rsdft_set_autotune(rsdft_ctx *ctx, int on);
 
 #ifdef __cplusplus
 }

@@ -295,9 +295,56 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     return RSDFT_OK;
 }
 
+rsdft_status autotune_pick(rsdft_ctx *ctx, const std::string &key, int ncand, int fallback, cudaStream_t st,
+                           const std::function<rsdft_status(int)> &run, int *chosen) {
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end() || !ctx->autotune || ncand <= 1) {
+        const int c = it != ctx->tuned.end() ? it->second : fallback;
+        *chosen = c;
+        return run(c);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RS_CUDA(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, RSDFT_E_CUDA, "cudaEventCreate failed");
+    }
+    int best = fallback;
+    float best_ms = 0.0f;
+    rsdft_status r = RSDFT_OK;
+    for (int c = 0; c < ncand && r == RSDFT_OK; ++c) {
+        cudaEventRecord(e0, st);
+        r = run(c);
+        cudaEventRecord(e1, st);
+        if (r != RSDFT_OK) break;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            r = fail(ctx, RSDFT_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != RSDFT_OK) return r;
+    ctx->tuned[key] = best;
+    *chosen = best;
+    return best == ncand - 1 ? RSDFT_OK : run(best);   // the winner's result last
+}
+
 }  // namespace rsdft
 
 using namespace rsdft;
+
+extern "C" rsdft_status rsdft_set_autotune(rsdft_ctx *ctx, int on) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    ctx->autotune = on != 0;
+    if (!ctx->autotune) ctx->tuned.clear();
+    return RSDFT_OK;
+}
 
 extern "C" {
 

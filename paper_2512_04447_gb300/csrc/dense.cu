@@ -9,6 +9,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <mutex>
+
 #include "rsdft_internal.h"
 
 namespace rsdft {
@@ -57,15 +59,15 @@ __global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double t
     }
 }
 
-// Factor columns kb..kb+nb-1 (rows kb..k-1, nb <= 32), in place in the lower
-// triangle.  Every CTA factors the nb x nb diagonal block in shared memory
-// (column c is dropped when its Schur pivot is <= the floor: l_cc = 1 and
-// L[c+1:, c] = 0); CTA 0 writes it back with the drop flags.  Then each warp
+// Factor columns kb..kb+nb-1 (rows kb..k-1, nb <= 32) in the lower triangle.
+// Every CTA factors the nb x nb diagonal block in shared memory (column c is
+// dropped when its Schur pivot is <= the floor: l_cc = 1 and L[c+1:, c] = 0);
+// CTA 0 writes it to diag_out with the drop flags.  Then each warp
 // solves one row i below the block, l_i = a_i L11^-H, by forward substitution
 // with lane c holding column c: the rows spread over the CTAs (one FP64 chain
 // of nb steps per row) instead of one CTA walking the whole panel.
 __global__ void __launch_bounds__(256)
-k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop) {
+k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop, double2 *diag_out) {
     __shared__ double2 sD[NBK][NBK + 1];
     __shared__ double s_l[NBK], s_il[NBK];   // pivots and their reciprocals
     __shared__ int s_drop[NBK];
@@ -108,11 +110,11 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
         }
         __syncthreads();
     }
+    // the factored block goes to scratch, not back into a: other CTAs of this
+    // launch may not have read the original block yet (k_chol_update, the next
+    // launch, copies it into place)
     if (blockIdx.x == 0) {
-        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-            const int r = t / nb, c = t % nb;
-            if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = sD[r][c];
-        }
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) diag_out[t] = sD[t / nb][t % nb];
         for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
     }
     // rows below the diagonal block: warp per row, lane c = column kb + c
@@ -140,9 +142,18 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
     }
 }
 
-// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb.
-__global__ void k_chol_update(double2 *a, int k, int ld, int kb, int nb) {
+// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb;
+// block (0, 0) also stores the panel's factored diagonal block from diag
+// (lower triangle) into a.  Launched with at least one block.
+__global__ void k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restrict__ diag) {
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int r = t / nb, c = t % nb;
+            if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = diag[t];
+        }
+    }
     const int t0 = kb + nb;
+    if (t0 >= k) return;
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
     const int i0 = t0 + ti * 32, j0 = t0 + tj * 32;
@@ -489,6 +500,11 @@ struct GridSync {
 };
 
 __device__ __forceinline__ double2 ldcg2(const double2 *p) { return __ldcg(p); }
+
+std::mutex &coop_mutex() {
+    static std::mutex m;
+    return m;
+}
 
 // Grid barrier on a monotonic arrival counter (zeroed before the launch): the
 // e-th barrier of the launch completes when count reaches nblocks * (e + 1).
@@ -1068,22 +1084,29 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     }
     const int ld = k;
     bool coop_done = false;
+    std::unique_lock<std::mutex> coop_lock;
     {
-        // one cooperative launch for all Householder steps
-        static int occ = -1;
-        if (occ < 0) {
-            int attr = 0;
-            cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, 0);
+        // one cooperative launch for all Householder steps (occupancy queried once,
+        // thread-safe static initialisation)
+        static const int occ = [] {
+            int dev = 0, coop = 0, o = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
             // the opt-in shared memory size first: the occupancy query below
             // asks for more than the default 48 KB
-            if (attr == 0 ||
+            if (coop == 0 ||
                 cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * MAX_K_COOP * sizeof(double2)) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_coop, 256,
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tridiag_coop, 256,
                                                               3 * MAX_K_COOP * sizeof(double2)) != cudaSuccess)
-                occ = 0;
+                o = 0;
             cudaGetLastError();
-        }
+            return o;
+        }();
+        // cooperative grids of different contexts (batched cells on other streams)
+        // never run at the same time: the lock is held until this call's final
+        // stream synchronisation
+        if (occ > 0 && k <= MAX_K_COOP) coop_lock = std::unique_lock<std::mutex>(coop_mutex());
         if (occ > 0 && k <= MAX_K_COOP) {
             int nb = std::max(1, std::min(ctx->num_sms * std::min(occ, 1), cdiv((long long)k * k, 1024)));
             GridSync *gs = reinterpret_cast<GridSync *>(w.gsync);
@@ -1100,6 +1123,8 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
                 coop_done = true;
             } else {
                 cudaGetLastError();   // fall back to one launch per phase
+                ++ctx->coop_fallbacks;
+                ctx->coop_last_error = (int)e;
             }
         }
     }
@@ -1128,14 +1153,18 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     count_launch(ctx);
     {
         const size_t ii_smem = (size_t)6 * k * sizeof(double);
+        static std::mutex ii_mutex;
         static size_t ii_smem_max = 0;
-        if (ii_smem > 48 * 1024 && ii_smem > ii_smem_max && ii_smem <= 200 * 1024) {
-            if (cudaFuncSetAttribute(k_inverse_iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)ii_smem) == cudaSuccess)
+        bool use_smem = ii_smem <= 48 * 1024;
+        if (!use_smem && ii_smem <= 200 * 1024) {
+            std::lock_guard<std::mutex> g(ii_mutex);
+            if (ii_smem > ii_smem_max &&
+                cudaFuncSetAttribute(k_inverse_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ii_smem) ==
+                    cudaSuccess)
                 ii_smem_max = ii_smem;
             cudaGetLastError();
+            use_smem = ii_smem <= ii_smem_max;
         }
-        const bool use_smem = ii_smem <= 48 * 1024 || ii_smem <= ii_smem_max;
         k_inverse_iter<<<nkeep, 32, use_smem ? ii_smem : 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr,
                                                                    w.fac, w.zt, use_smem ? 1 : 0);
     }
@@ -1186,15 +1215,14 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     count_launch(ctx);
     for (int kb = 0; kb < k; kb += NBK) {
         const int nb = std::min(NBK, k - kb);
+        // w.Km is free until the compaction below: scratch for the factored block
         k_chol_panel<<<std::max(1, cdiv(k - kb - nb, 8)), 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4,
-                                                                         w.drop);
+                                                                         w.drop, w.Km);
         count_launch(ctx);
         const int rest = k - kb - nb;
-        if (rest > 0) {
-            dim3 g(cdiv(rest, 32), cdiv(rest, 32));
-            k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb);
-            count_launch(ctx);
-        }
+        dim3 g(std::max(1, cdiv(rest, 32)), std::max(1, cdiv(rest, 32)));
+        k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.Km);
+        count_launch(ctx);
     }
     k_keep_scan<<<1, 1, 0, st>>>(w.drop, k, w.keep);
     count_launch(ctx);

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <string>
+
 #include "rsdft_internal.h"
 
 namespace rsdft {
@@ -228,11 +230,19 @@ rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> 
     const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
     if (na <= 0 || nb <= 0) return RSDFT_OK;
     if (hermitian && na != nb) return fail(ctx, RSDFT_E_INVALID, "hermitian gram needs na == nb");
-    switch (pick_p(na, nb)) {
-        case 2: return gram_launch<V, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-        case 3: return gram_launch<V, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-        default: return gram_launch<V, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-    }
+    // tile edge 16 P, P in {2, 3, 4}: the least-padding rule, or the autotuner's pick
+    auto run = [&](int c) -> rsdft_status {
+        switch (c + 2) {
+            case 2: return gram_launch<V, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            case 3: return gram_launch<V, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            default: return gram_launch<V, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+        }
+    };
+    // shapes in buckets of 32 (the subspace size changes as bands lock)
+    const std::string key = std::string(sizeof(V) == 8 ? "gram32 " : "gram64 ") + std::to_string(cdiv(na, 32)) +
+                            " " + std::to_string(cdiv(nb, 32)) + (hermitian ? " h" : " g");
+    int chosen = 0;
+    return autotune_pick(ctx, key, 3, pick_p(na, nb) - 2, st, run, &chosen);
 }
 
 rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double2 *g, int ldg,
@@ -372,12 +382,21 @@ rsdft_status rotate_t(rsdft_ctx *ctx, const RowBlocksT<V> &Y, const double2 *c, 
         const int pad = cdiv(m, 16 * pb) * 16 * pb - m;
         if (pad < bestpad) { bestpad = pad; best = pb; }
     }
-    switch (best) {
-        case 1: return rotate_launch<V, 1>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
-        case 2: return rotate_launch<V, 2>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
-        case 3: return rotate_launch<V, 3>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
-        default: return rotate_launch<V, 4>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
-    }
+    auto run = [&](int cand) -> rsdft_status {
+        switch (cand + 1) {
+            case 1: return rotate_launch<V, 1>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+            case 2: return rotate_launch<V, 2>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+            case 3: return rotate_launch<V, 3>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+            default: return rotate_launch<V, 4>(ctx, Y, c, ldc, m, base, sign, out0, out1, st);
+        }
+    };
+    // an update in place (base) may not run twice: the least-padding rule only
+    if (base) return run(best - 1);
+    const int k = Y.cnt[0] + Y.cnt[1] + Y.cnt[2];
+    const std::string key = std::string(sizeof(V) == 8 ? "rot32 " : "rot64 ") + std::to_string(cdiv(k, 32)) +
+                            " " + std::to_string(cdiv(m, 32)) + (out1 ? " p" : " x");
+    int chosen = 0;
+    return autotune_pick(ctx, key, 4, best - 1, st, run, &chosen);
 }
 
 rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ldc, int m,

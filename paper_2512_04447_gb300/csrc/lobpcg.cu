@@ -9,6 +9,8 @@
 // The host reads back one small vector per iteration (residual norms) plus
 // the kept-column count of the Cholesky.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <type_traits>
 
@@ -571,6 +573,7 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
     double *hres = w.hbuf;
     RunState rs;
     int it_mixed = 0;
+    const long long fallbacks0 = ctx->coop_fallbacks;
     rsdft_status r = RSDFT_OK;
     if (o.precision == RSDFT_MIXED) {
         // mixed form: FP32 data path until switch_tol (or stagnation), then FP64
@@ -603,6 +606,8 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
         stats->iterations_mixed = it_mixed;
         stats->converged = rs.converged ? 1 : 0;
         stats->dropped = rs.dropped;
+        stats->coop_fallbacks = (int)(ctx->coop_fallbacks - fallbacks0);
+        stats->coop_last_error = stats->coop_fallbacks ? ctx->coop_last_error : 0;
     }
     if (eig_host) RS_CUDA(ctx, cudaMemcpyAsync(eig_host, w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaStreamSynchronize(st));
@@ -648,6 +653,57 @@ rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lo
         return fail(ctx, RSDFT_E_INVALID, "unknown preconditioner");
     if (stats) *stats = rsdft_lobpcg_stats{};
     return lobpcg_run(ctx, (double2 *)x_dev, nband, o, eig_host, resnorm_host, stats, as_stream(stream));
+}
+
+rsdft_status rsdft_lobpcg_batched(rsdft_ctx *const *ctxs, int ncell, void *const *x_dev, const int *nband,
+                                  const rsdft_lobpcg_opts *opts, double *const *eig_host,
+                                  double *const *res_host, rsdft_lobpcg_stats *stats, int max_concurrent,
+                                  int *failed_cell) {
+    if (failed_cell) *failed_cell = -1;
+    if (ncell < 0 || (ncell > 0 && (!ctxs || !x_dev || !nband)))
+        return fail(nullptr, RSDFT_E_INVALID, "bad batch arguments");
+    for (int c = 0; c < ncell; ++c)
+        if (!ctxs[c]) return fail(nullptr, RSDFT_E_INVALID, "cell %d: ctx is NULL", c);
+    if (ncell == 0) return RSDFT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "cudaGetDevice failed");
+    // the cells' streams do not order against the caller's work: let everything
+    // issued so far (e.g. the uploads of the orbital blocks) finish first
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return fail(nullptr, RSDFT_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    const int nthr = std::max(1, std::min(ncell, max_concurrent <= 0 ? 8 : max_concurrent));
+    std::vector<rsdft_status> status(ncell, RSDFT_OK);
+    std::atomic<int> next{0};
+    // one host thread and one stream per concurrent cell; cells are handed out
+    // in order, so the cells in flight at any time are consecutive
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t st = nullptr;
+        const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        for (int c; (c = next.fetch_add(1)) < ncell;) {
+            if (!have_stream) {
+                status[c] = fail(ctxs[c], RSDFT_E_CUDA, "could not create a stream for the batch");
+                continue;
+            }
+            status[c] = rsdft_lobpcg(ctxs[c], x_dev[c], nband[c], opts ? &opts[c] : nullptr,
+                                     eig_host ? eig_host[c] : nullptr,
+                                     res_host ? res_host[c] : nullptr, stats ? &stats[c] : nullptr, st);
+            if (status[c] == RSDFT_OK && cudaStreamSynchronize(st) != cudaSuccess)
+                status[c] = fail(ctxs[c], RSDFT_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (have_stream) cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(nthr);
+    for (int t = 0; t < nthr; ++t) pool.emplace_back(worker);
+    for (auto &t : pool) t.join();
+    for (int c = 0; c < ncell; ++c) {
+        if (status[c] != RSDFT_OK) {
+            if (failed_cell) *failed_cell = c;
+            return status[c];
+        }
+    }
+    return RSDFT_OK;
 }
 
 }  // extern "C"

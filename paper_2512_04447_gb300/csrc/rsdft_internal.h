@@ -5,6 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <functional>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/rsdft.h"
@@ -75,7 +78,7 @@ struct Workspace {
     unsigned int *gsync = nullptr;  // grid-barrier state of the cooperative kernels
     // tensor-core Gram: BF16 hi/lo operands, FP32 split partials, error flag
     void *tcbuf = nullptr;  size_t tc_bytes = 0;
-    float *tcpart = nullptr;  size_t tcpart_elems = 0;
+    float2 *tcpart = nullptr;  size_t tcpart_elems = 0;   // tensor-core split-K partials (complex)
     int *tcerr = nullptr;
     void *tcrot = nullptr;  size_t tcrot_bytes = 0;   // split rotation coefficients
     // per-band vectors [cap_band]
@@ -127,6 +130,10 @@ struct rsdft_ctx {
     rsdft::ScfWork scf;
     rsdft::Profiler prof;
     long long launches = 0;          // every kernel launched on this context
+    long long coop_fallbacks = 0;    // tridiagonalisations that could not launch cooperatively
+    int coop_last_error = 0;         // cudaError_t of the last such launch
+    bool autotune = false;           // time the tile candidates on the first call of a shape
+    std::map<std::string, int> tuned;   // shape key -> chosen candidate
     std::string err;
 };
 
@@ -243,7 +250,19 @@ rsdft_status rotate_tc_ortho(rsdft_ctx *ctx, int m, int na, const double2 *c, fl
 rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c, int ldc, int m,
                        float2 *out0, float2 *out1, cudaStream_t st);
 
+// ---- autotuner (context.cu) --------------------------------------------------
+// With ctx->autotune set, the first call of a shape runs each candidate once on
+// the stream, timed with CUDA events, and remembers the fastest under `key`
+// (later calls reuse it; without autotune the closed-form choice is used).
+// run(i) launches candidate i; the winner is run last so that its result is the
+// one left in the outputs.  Only for calls whose outputs do not alias inputs.
+rsdft_status autotune_pick(rsdft_ctx *ctx, const std::string &key, int ncand, int fallback, cudaStream_t st,
+                           const std::function<rsdft_status(int)> &run, int *chosen);
+
 // ---- dense core (dense.cu) ----------------------------------------------------
+// Held from a cooperative launch until the stream that launched it has
+// synchronised: cooperative grids of different contexts never overlap.
+std::mutex &coop_mutex();
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,
                            int nkeep, double pivot_tol, double *lam_dev, double2 *c_out,
                            int *ndropped, cudaStream_t st);

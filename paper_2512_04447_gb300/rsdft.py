@@ -54,7 +54,7 @@ class LobpcgOpts(C.Structure):
 
 class LobpcgStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("iterations_mixed", C.c_int), ("converged", C.c_int),
-                ("dropped", C.c_int),
+                ("dropped", C.c_int), ("coop_fallbacks", C.c_int), ("coop_last_error", C.c_int),
                 ("ms_hpsi", C.c_double), ("ms_precond", C.c_double), ("ms_gram", C.c_double),
                 ("ms_dense", C.c_double), ("ms_rotate", C.c_double), ("ms_other", C.c_double)]
 
@@ -102,6 +102,9 @@ _PROTOS = {
     "rsdft_eigh": (ip, [vp, vp, ip, ip, vp, vp, vp]),
     "rsdft_lobpcg_default_opts": (None, [C.POINTER(LobpcgOpts)]),
     "rsdft_lobpcg": (ip, [vp, vp, ip, C.POINTER(LobpcgOpts), vp, vp, C.POINTER(LobpcgStats), vp]),
+    "rsdft_set_autotune": (ip, [vp, ip]),
+    "rsdft_lobpcg_batched": (ip, [vp, ip, vp, vp, C.POINTER(LobpcgOpts), vp, vp, C.POINTER(LobpcgStats), ip,
+                                  C.POINTER(C.c_int)]),
     "rsdft_scf_default_opts": (None, [C.POINTER(ScfOpts)]),
     "rsdft_scf_init": (ip, [vp, ip, C.POINTER(ScfOpts), vp]),
     "rsdft_scf_step": (ip, [vp, vp, ip, C.POINTER(ScfOpts), C.POINTER(ScfOut), vp, vp, vp]),
@@ -189,6 +192,34 @@ def gram_static(a, b, g, scale: float) -> None:
         raise RsdftError(st, lib().rsdft_last_error(None).decode())
 
 
+def lobpcg_batched(ctxs, xs, opts, max_concurrent: int = 0):
+    """rsdft_lobpcg_batched: LOBPCG on independent cells concurrently (one stream
+    and host thread per cell in flight).  ctxs: Context per cell; xs: device
+    [nband][n] complex128 blocks (in/out); opts: one LobpcgOpts for all cells or
+    a list with one per cell.  Returns (eigs, resnorms, stats, status,
+    failed_cell); RSDFT_E_NOT_CONVERGED from a cell is returned, not raised."""
+    n = len(ctxs)
+    assert len(xs) == n
+    per = list(opts) if isinstance(opts, (list, tuple)) else [opts] * n
+    assert len(per) == n
+    oarr = (LobpcgOpts * n)(*per)
+    h = (C.c_void_p * n)(*[c._h for c in ctxs])
+    xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    nb = (C.c_int * n)(*[int(x.shape[0]) for x in xs])
+    eigs = [np.zeros(int(x.shape[0])) for x in xs]
+    ress = [np.zeros(int(x.shape[0])) for x in xs]
+    ep = (C.c_void_p * n)(*[_ptr(e) for e in eigs])
+    rp = (C.c_void_p * n)(*[_ptr(r) for r in ress])
+    stats = (LobpcgStats * n)()
+    failed = C.c_int(-1)
+    st = lib().rsdft_lobpcg_batched(h, n, xp, nb, oarr, ep, rp, stats, int(max_concurrent), C.byref(failed))
+    if st not in (OK, E_NOT_CONVERGED):
+        ctx = ctxs[failed.value] if 0 <= failed.value < n else None
+        msg = lib().rsdft_last_error(ctx._h if ctx else None).decode()
+        raise RsdftError(st, f"cell {failed.value}: {msg}")
+    return eigs, ress, list(stats), st, failed.value
+
+
 class Context:
     """rsdft_create / rsdft_destroy and the calls bound to a context."""
 
@@ -270,6 +301,9 @@ class Context:
     def gram(self, a, b, g):
         self._check(lib().rsdft_gram(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(g),
                                      _stream()))
+
+    def set_autotune(self, on: bool = True):
+        self._check(lib().rsdft_set_autotune(self._h, 1 if on else 0))
 
     def gram_bf16x3(self, a, b, g):
         self._check(lib().rsdft_gram_bf16x3(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0],

@@ -140,11 +140,14 @@ def batched_cells(ncell: int = 32) -> List[Workload]:
         h = float(rng.uniform(0.2, 0.25))
         L = N * h
         if c % 2 == 0:
-            reps = 1 if L < 11.0 else 2
+            # diamond supercell count from the diamond lattice constant (6.74 bohr)
+            reps = max(1, int(round(L / 6.74)))
             pos = diamond_sites(L / reps, reps)
             Z, ne_per_atom = 4.0, 4.0
         else:
-            reps = 2 if L < 11.0 else 3
+            # a 2x2x2 bcc supercell (16 atoms): 48 occupied bands, so the band
+            # count keeps its buffer above the occupied ones
+            reps = 2
             pos = bcc_sites(L / reps, reps)
             Z, ne_per_atom = 6.0, 6.0
         natom = pos.shape[0]
