@@ -13,6 +13,9 @@
 #include <algorithm>
 #include <cmath>
 
+#include <mutex>
+#include <vector>
+
 #include "rsdft_internal.h"
 
 namespace rsdft {
@@ -144,6 +147,13 @@ __device__ __forceinline__ void bfly(V *s, int base, int step, int j, int twstep
 // x / d for x < 2^16 from the multiply-high divisor of d (mag = 0 means d = 1).
 __device__ __forceinline__ int qdiv(int x, unsigned mag) { return mag ? (int)__umulhi((unsigned)x, mag) : x; }
 
+// xy planes live in shared memory with an odd row stride RS = Nx | 1 (complex
+// values): the lines of both transform directions are then read by consecutive
+// threads without bank conflicts (successive rows start two banks apart).
+__device__ __forceinline__ int plane_rs(int Nx) { return Nx | 1; }
+// shared-memory index of plane element i = y Nx + x
+__device__ __forceinline__ int pidx(int i, int Nx, int RS, unsigned nxmag) { return i + qdiv(i, nxmag) * (RS - Nx); }
+
 // nlmag: multiply-high divisor of nlines.  Quotients and remainders of the
 // index decomposition use it instead of integer division (total < 2^16).
 template <typename V, bool INV>
@@ -226,9 +236,11 @@ k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src
     const size_t n = (size_t)Nx * Ny * Nz;
     const size_t plane = (size_t)Nx * Ny;
     const size_t off = (size_t)z * plane;
+    const int RS = plane_rs(Nx);
+    const unsigned nxm = tb.ax[0].nmag;
     if (SRC == Src::Plain) {
         const V *in = src + band * n + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = in[i];
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[pidx(i, Nx, RS, nxm)] = in[i];
     } else if (SRC == Src::Residual) {
         const int b = act[band];
         const T th = (T)theta[b];
@@ -236,17 +248,18 @@ k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src
         const V *x = src2 + b * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
             V h = hx[i], v = x[i];
-            s_plane[i] = mk<V>(h.x - th * v.x, h.y - th * v.y);
+            s_plane[pidx(i, Nx, RS, nxm)] = mk<V>(h.x - th * v.x, h.y - th * v.y);
         }
     } else {
         const double *in = rsrc + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = mk<V>((T)in[i], (T)0);
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x)
+            s_plane[pidx(i, Nx, RS, nxm)] = mk<V>((T)in[i], (T)0);
     }
     __syncthreads();
-    fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, Nx, 1, false);
-    fft_lines<V, false>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, Nx, true);
+    fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, RS, 1, true);
+    fft_lines<V, false>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, RS, true);
     V *out = dst + band * n + off;
-    for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) out[i] = s_plane[i];
+    for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) out[i] = s_plane[pidx(i, Nx, RS, nxm)];
 }
 
 // ---- z pass with the per-G factor ------------------------------------------------
@@ -316,16 +329,18 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
     const size_t plane = (size_t)Nx * Ny;
     const size_t off = (size_t)z * plane;
     const V *in = buf + band * n + off;
-    for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[i] = in[i];
+    const int RS = plane_rs(Nx);
+    const unsigned nxm = tb.ax[0].nmag;
+    for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[pidx(i, Nx, RS, nxm)] = in[i];
     __syncthreads();
-    fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, Nx, true);
-    fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, Nx, 1, false);
+    fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, RS, true);
+    fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, RS, 1, true);
     if (EPI == Epi::Plain) {
         V *o = out + band * n + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = s_plane[i];
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = s_plane[pidx(i, Nx, RS, nxm)];
     } else if (EPI == Epi::Real) {
         double *o = rout + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = (double)s_plane[i].x;
+        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) o[i] = (double)s_plane[pidx(i, Nx, RS, nxm)].x;
     } else {
         const V *ps = psi + band * n + off;
         const T *vv = v + off;
@@ -333,7 +348,7 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
         const V *pb = p + (size_t)band * np;
         // E_aj <beta_aj|psi> of this band, staged once per CTA after the plane
         // (when it fits; else read from global memory)
-        V *s_pe = s_plane + plane;
+        V *s_pe = s_plane + (size_t)Ny * RS;
         if (stage_pe) {
             for (int q = threadIdx.x; q < np; q += blockDim.x) {
                 const V c = pb[q];
@@ -344,7 +359,7 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
         }
         V *o = out + band * n + off;
         for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
-            V t = s_plane[i];
+            V t = s_plane[pidx(i, Nx, RS, nxm)];
             V y = ps[i];
             T vi = vv[i];
             T ax = t.x + vi * y.x, ay = t.y + vi * y.y;
@@ -439,7 +454,7 @@ __global__ void k_to_float(const double *__restrict__ in, long long n, float *__
 
 // ---- launchers -------------------------------------------------------------------------
 template <typename V> static size_t plane_bytes(const rsdft_ctx *ctx) {
-    return (size_t)ctx->N[0] * ctx->N[1] * sizeof(V);
+    return (size_t)(ctx->N[0] | 1) * ctx->N[1] * sizeof(V);   // odd row stride
 }
 template <typename V> static size_t slab_bytes(const rsdft_ctx *ctx) {
     return (size_t)ctx->N[0] * ctx->N[2] * sizeof(V);
@@ -447,9 +462,20 @@ template <typename V> static size_t slab_bytes(const rsdft_ctx *ctx) {
 
 constexpr size_t MAX_DYN_SMEM = 227 * 1024;   // largest dynamic shared memory of one CTA
 
+// The attribute is per function and process-wide, so it is raised once to the
+// largest size (occupancy follows each launch's own dynamic size); lowering it
+// per launch would race with launches of other contexts on other threads.
 template <typename K> static rsdft_status set_smem(rsdft_ctx *ctx, K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        RS_CUDA(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes <= 48 * 1024) return RSDFT_OK;
+    if (bytes > MAX_DYN_SMEM) return fail(ctx, RSDFT_E_INVALID, "plane needs %zu B of shared memory", bytes);
+    static std::mutex mu;
+    static std::vector<const void *> done;
+    std::lock_guard<std::mutex> g(mu);
+    const void *key = reinterpret_cast<const void *>(kernel);
+    if (std::find(done.begin(), done.end(), key) == done.end()) {
+        RS_CUDA(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_DYN_SMEM));
+        done.push_back(key);
+    }
     return RSDFT_OK;
 }
 
