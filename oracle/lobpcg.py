@@ -14,7 +14,8 @@ block form (the readings are listed in the design notes):
     b. Active set A = {b : res_b > lock_tol} (soft locking: a band whose
        residual is at round-off level keeps its place in X but contributes
        no W or P column, since its preconditioned residual is noise).
-    c. W = T_prec(R_A) (Teter-Payne-Allan, or identity), then W <- W - X <X|W>
+    c. W = T_prec(R_A) (Teter-Payne-Allan, TPA plus the learned network
+       correction of ``oracle.precond``, or identity), then W <- W - X <X|W>
        (Hetmaniuk-Lehoucq orthogonalisation against X); HW = H W.
     d. Normalise the columns of W and P_A, scaling HW and HP_A alike.
     e. Y = [X W P_A] (first iteration [X W]), HY = [HX HW HP_A];
@@ -46,6 +47,7 @@ import scipy.fft as sfft
 
 from .hamiltonian import Hamiltonian, inner
 from .linalg import hermitise, rayleigh_ritz
+from .precond import learned_apply, standardise
 
 
 LOCK_TOL = 1e-10     # residual (Ha) at or below which a band is soft-locked
@@ -110,7 +112,8 @@ def lobpcg(ham: Hamiltonian, X0: np.ndarray, maxit: int, tol: float = 0.0,
            nconv: Optional[int] = None, precond: str = "tpa",
            P0: Optional[np.ndarray] = None, HP0: Optional[np.ndarray] = None,
            initial_rr: bool = True, lock_tol: float = LOCK_TOL,
-           pivot_tol: float = PIVOT_TOL) -> LobpcgResult:
+           pivot_tol: float = PIVOT_TOL, nn_weights: Optional[np.ndarray] = None,
+           nn_hidden: int = 8) -> LobpcgResult:
     dV = ham.dV
     m = X0.shape[0]
     nconv = m if nconv is None else nconv
@@ -136,6 +139,10 @@ def lobpcg(ham: Hamiltonian, X0: np.ndarray, maxit: int, tol: float = 0.0,
             break
         if precond == "tpa":
             W = tpa_precondition(ham, R[act], X[act])
+        elif precond == "learned":
+            # TPA plus the network correction (oracle.precond, residual form)
+            W = learned_apply(R[act], tpa_precondition(ham, R[act], X[act]), standardise(ham.v),
+                              nn_weights, ham.grid.shape, nn_hidden)
         elif precond == "none":
             W = R[act].copy()
         else:

@@ -24,6 +24,7 @@ import numpy as np
 # draw is independent of the order in which the others are made.
 _STREAM_EKB = 0
 _STREAM_X0 = 1
+_STREAM_NN = 2
 
 
 def diamond_sites(a: float, reps: int) -> np.ndarray:
@@ -59,6 +60,22 @@ def draw_x0(seed: int, nband: int, npts: int) -> np.ndarray:
     rng = np.random.default_rng([seed, _STREAM_X0])
     re_im = rng.standard_normal((nband, npts, 2))
     return re_im.view(np.complex128)[..., 0]
+
+
+def draw_nn_weights(seed: int, hidden: int = 8) -> np.ndarray:
+    """Initial weights of the preconditioner network (four 3x3x3 convolutions,
+    channels 2 -> hidden -> hidden -> hidden -> 1, each layer [27][cin][cout]),
+    flat float64: normal with standard deviation 1/sqrt(27 cin) for the first
+    three layers and zero for the last (the network starts as no correction)."""
+    rng = np.random.default_rng([seed, _STREAM_NN])
+    chans = [(2, hidden), (hidden, hidden), (hidden, hidden), (hidden, 1)]
+    out = []
+    for l, (ci, co) in enumerate(chans):
+        if l == len(chans) - 1:
+            out.append(np.zeros(27 * ci * co))
+        else:
+            out.append(rng.standard_normal(27 * ci * co) / np.sqrt(27.0 * ci))
+    return np.concatenate(out)
 
 
 @dataclasses.dataclass
@@ -126,6 +143,32 @@ def bcc128_120(seed: int = 0) -> Workload:
                     Z=6.0, nband=460, n_electrons=768.0, kT=0.01, seed=seed, maxit=200)
 
 
+def diamond8_32(seed: int = 0) -> Workload:
+    """8 C in one diamond-cubic cell (a = L = 6.74 bohr) on a 32^3 grid: the
+    spacing (0.2106 bohr) and chemistry of the 64-atom 64^3 cell; 20 bands (16
+    occupied).  A training cell of the learned preconditioner."""
+    return Workload("diamond8_32", _cubic(6.74), (32, 32, 32), diamond_sites(6.74, 1),
+                    Z=4.0, nband=20, n_electrons=32.0, seed=seed, maxit=200)
+
+
+def bcc2_30(seed: int = 0) -> Workload:
+    """2 atoms in one bcc cell (a = L = 5.98 bohr, Z = 6) on a 30^3 grid: the
+    spacing (0.1993 bohr) and chemistry of the 128-atom 120^3 metal; 8 bands
+    (6 occupied), Fermi-Dirac kT = 0.01.  The projectors are cut at 2.9 bohr,
+    just below half the cell edge.  A training cell of the learned
+    preconditioner."""
+    return Workload("bcc2_30", _cubic(5.98), (30, 30, 30), bcc_sites(5.98, 1), Z=6.0,
+                    rcut=2.9, nband=8, n_electrons=12.0, kT=0.01, seed=seed, maxit=200)
+
+
+def bcc16_60(seed: int = 0) -> Workload:
+    """16 atoms (2x2x2 bcc, a = 5.98, L = 11.96, Z = 6) on a 60^3 grid (the
+    128-atom metal's spacing), 56 bands (48 occupied), kT = 0.01: the reduced
+    metal cell on which the learned preconditioner is judged against TPA."""
+    return Workload("bcc16_60", _cubic(11.96), (60, 60, 60), bcc_sites(5.98, 2), Z=6.0,
+                    nband=56, n_electrons=96.0, kT=0.01, seed=seed, maxit=200)
+
+
 FIVE_SMOOTH_BATCH_GRIDS = (32, 36, 40, 45, 48, 50, 54, 60, 64)
 
 
@@ -175,4 +218,7 @@ REGISTRY = {
     "diamond64_64": diamond64_64,
     "diamond216_96": diamond216_96,
     "bcc128_120": bcc128_120,
+    "diamond8_32": diamond8_32,
+    "bcc2_30": bcc2_30,
+    "bcc16_60": bcc16_60,
 }
