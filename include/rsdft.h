@@ -57,7 +57,9 @@ typedef enum {
 } rsdft_status;
 
 typedef enum { RSDFT_FP64 = 0, RSDFT_MIXED = 1 } rsdft_precision;
-typedef enum { RSDFT_PRECOND_NONE = 0, RSDFT_PRECOND_TPA = 1 } rsdft_precond;
+/* RSDFT_PRECOND_LEARNED: TPA plus the learned network correction (weights set
+ * with rsdft_set_precond_weights; RSDFT_E_INVALID without them). */
+typedef enum { RSDFT_PRECOND_NONE = 0, RSDFT_PRECOND_TPA = 1, RSDFT_PRECOND_LEARNED = 2 } rsdft_precond;
 
 /* Lattice vectors as rows, bohr.  Only diagonal (orthorhombic) cells are
  * accepted; off-diagonal entries must be 0 (RSDFT_E_INVALID otherwise). */
@@ -166,6 +168,15 @@ rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int
  * complex128.  Relative error about 1e-5 of max |G|. */
 rsdft_status rsdft_gram_bf16x3(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb,
                                void *g_dev, void *stream);
+
+/* The Hermitian pair of the LOBPCG Rayleigh-Ritz step on the tensor cores:
+ * G_S = dV Y^H Y and G_H = dV Y^H (HY) as one split-BF16 GEMM of Y against
+ * [Y; HY], computing only the tiles that hold entries on or above the
+ * diagonal; entries below it are the conjugates of their mirrors (exactly
+ * Hermitian).  y_dev, hy_dev: [k][n] complex64; gs_dev, gh_dev: [k][k]
+ * complex128, row-major. */
+rsdft_status rsdft_gram_sh_bf16x3(rsdft_ctx *ctx, const void *y_dev, const void *hy_dev, int k, void *gs_dev,
+                                  void *gh_dev, void *stream);
 
 /* Ritz rotation of a complex64 block on the tensor cores (the mixed form's
  * rotation, SCF task (2)): with Y = y_dev [k][n] complex64 and C = c_dev [k][m]
@@ -371,6 +382,70 @@ long long rsdft_launch_count(const rsdft_ctx *ctx);
  * summation order, so results agree to rounding.  on = 0 switches it off and
  * forgets the choices. */
 rsdft_status rsdft_set_autotune(rsdft_ctx *ctx, int on);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner (the learned form of the LOBPCG preconditioner; the
+ * paper's LOBPCG uses a kinetic-energy preconditioner, here Teter-Payne-Allan).
+ *
+ * w_b = TPA(r_b) + s_b (NN(Re r_b / s_b) + i NN(Im r_b / s_b)),
+ * s_b = sqrt(sum_p |r_b(p)|^2 / n) (no correction where s_b = 0).
+ * NN maps a real plane u to a real plane: input channels (u, u vhat) with
+ * vhat = (V - mean V) / std V of the context's current potential, then four
+ * periodic 3x3x3 convolutions without biases, channels
+ * 2 -> RSDFT_NN_HIDDEN -> RSDFT_NN_HIDDEN -> RSDFT_NN_HIDDEN -> 1, tanh after
+ * the first three.  A convolution is out[co](p) = sum_ci sum_d
+ * w[tap(d)][ci][co] in[ci](p + d) over d in {-1,0,1}^3 with periodic wrap,
+ * tap(d) = (dz+1)*9 + (dy+1)*3 + (dx+1).  Weights: float32, the four layers one
+ * after the other, each [27][cin][cout]; RSDFT_NN_WEIGHTS in all.  The network
+ * computes in FP32.
+ */
+#define RSDFT_NN_HIDDEN 8
+#define RSDFT_NN_WEIGHTS (27 * (2 * RSDFT_NN_HIDDEN + 2 * RSDFT_NN_HIDDEN * RSDFT_NN_HIDDEN + RSDFT_NN_HIDDEN))
+
+/* Copy the network weights in (w_host: count = RSDFT_NN_WEIGHTS finite floats,
+ * else RSDFT_E_INVALID) or out (RSDFT_E_INVALID before any were set).
+ * Synchronous. */
+rsdft_status rsdft_set_precond_weights(rsdft_ctx *ctx, const float *w_host, long long count);
+rsdft_status rsdft_get_precond_weights(rsdft_ctx *ctx, float *w_host, long long count);
+
+/* w = base + the network correction of r (formula above), per band.
+ * r_dev, base_dev, w_dev: [nband][n] complex128; w may alias base, not r. */
+rsdft_status rsdft_precond_learned(rsdft_ctx *ctx, const void *r_dev, const void *base_dev, void *w_dev,
+                                   int nband, void *stream);
+
+/* Training samples from a block of normalised approximate orbitals x_dev
+ * ([nband][n] complex128, e.g. LOBPCG iterates): per band e = <x|H|x>,
+ * r = H x - e x, s = sqrt(sum |r|^2 / n), base = TPA(r) (T_b = <x|T|x>), and
+ * t perpendicular to x solving (I - x x^H)(H - e)(I - x x^H) t = -r by MINRES
+ * (Paige-Saunders) to relative residual rtol or maxit iterations (FP64);
+ * c = sign(Re<t|base>) ||base|| / ||t|| (t rescaled to the TPA norm, pointing
+ * along it: LOBPCG uses only the direction).  Writes float planes
+ * [2 nband][n] (real parts of every band, then imaginary parts): u = r / s,
+ * b = base / s, y = c t / s.
+ * iters_host (optional, [nband]): MINRES iterations per band.  Allocates and
+ * frees its own scratch (about 10 nband n complex128); synchronises. */
+rsdft_status rsdft_precond_samples(rsdft_ctx *ctx, const void *x_dev, int nband, double rtol, int maxit,
+                                   float *u_dev, float *b_dev, float *y_dev, int *iters_host, void *stream);
+
+/* Loss over all nsample planes (u, b, y: [nsample][n] float, device), the mean
+ * over planes of 1 - cos^2(p, y) = 1 - <p, y>^2 / (<p, p> <y, y>) with
+ * p = b + NN(u) (scale- and sign-free: LOBPCG uses only the span of a
+ * preconditioned residual), and its gradient in the weights (grad_host:
+ * RSDFT_NN_WEIGHTS floats), with the context's current weights and potential.
+ * Synchronises. */
+rsdft_status rsdft_precond_loss_grad(rsdft_ctx *ctx, const float *u_dev, const float *b_dev, const float *y_dev,
+                                     int nsample, float *loss_host, float *grad_host, void *stream);
+
+/* Train the context's weights (set initial ones first) on nsample float planes
+ * u, b, y ([nsample][n], device) from rsdft_precond_samples of this context's
+ * potential: Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr, fresh
+ * moments each call) for `steps` steps on mini-batches of `batch` samples taken
+ * cyclically (batch k = samples (k batch + j) mod nsample), minimising the
+ * loss of rsdft_precond_loss_grad.  loss_host (optional, [steps]): each
+ * step's batch loss before its update.  Synchronises. */
+rsdft_status rsdft_precond_train(rsdft_ctx *ctx, const float *u_dev, const float *b_dev, const float *y_dev,
+                                 long long nsample, int steps, int batch, float lr, float *loss_host,
+                                 void *stream);
 
 #ifdef __cplusplus
 }

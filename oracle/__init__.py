@@ -16,6 +16,9 @@ checked against the paper by eye:
                      subspace eigensolve (SCF task (3))
 * ``lobpcg``      -- Knyazev's LOBPCG with the Rayleigh-Ritz of Eq. 1 (SCF
                      tasks (2)-(3)) and the Teter-Payne-Allan preconditioner
+* ``precond``     -- the learned preconditioner: a residual-form periodic 3D
+                     convolutional network on TPA, its gradient, Adam, and the
+                     projected correction targets by MINRES
 * ``scf``         -- density, FFT Hartree, LDA (Slater + Perdew-Zunger 1981),
                      occupations (aufbau / Fermi-Dirac), Anderson mixing, and
                      one SCF step (the "Others" component of Fig. 1)

@@ -26,15 +26,23 @@ gives no network; the readings used here and in the CUDA path are:
   the 27 offsets d in {-1, 0, 1}^3 with periodic wrap; tap(d) = (dz + 1) 9 +
   (dy + 1) 3 + (dx + 1); grid index (iz Ny + iy) Nx + ix.  Weights are stored
   layer after layer, each as [27][cin][cout] (float32 on the device).
-* Training: loss = mean over samples and points of (b + NN(u) - y)^2, with u a
-  normalised residual plane, b its TPA plane and y the target plane; Adam
+* Training: per sample (a normalised residual plane u, its TPA plane b and the
+  target plane y) the loss is 1 - cos^2(b + NN(u), y) = 1 - <w, y>^2 / (<w, w>
+  <y, y>) with w = b + NN(u): LOBPCG uses only the span of a preconditioned
+  residual, so the loss ignores its scale and sign (a squared-error loss lets the
+  network lower it by shrinking w towards zero where y is hard to predict, which
+  cancels TPA and stalls LOBPCG); the batch loss is the mean over samples; Adam
   (Kingma and Ba 2015, Algorithm 1: beta1 0.9, beta2 0.999, eps 1e-8) on
   mini-batches taken in cyclic order (batch k = samples k B .. k B + B - 1
   modulo the sample count).
 * Target: t_b solves (I - x x^H)(H - e_b)(I - x x^H) t = -r_b, t perpendicular
   to x_b, by MINRES (Paige and Saunders 1975) to a relative residual of 1e-3;
-  the target plane is y = c_b t_b / s_b with c_b = Re<t_b|TPA(r_b)> / <t_b|t_b>,
-  the scale at which t_b best matches the TPA direction.
+  LOBPCG uses only the direction of a preconditioned residual, so the target
+  plane is t_b rescaled to the norm of TPA(r_b), with the sign that makes it
+  point along TPA(r_b): y = c_b t_b / s_b, c_b = sign(Re<t_b|TPA(r_b)>)
+  ||TPA(r_b)|| / ||t_b|| (a target that can shrink, like the least-squares
+  multiple of t_b, lets the network learn to cancel TPA where t_b is nearly
+  orthogonal to it).
 * Acceptance: the learned form is used only where it reaches the LOBPCG
   tolerance in fewer iterations than TPA from the same start; otherwise TPA.
 
@@ -155,11 +163,18 @@ def backward(acts: List[np.ndarray], g_out: np.ndarray, w: np.ndarray, shape: Se
 
 
 def loss_and_grad(u, b, y, vhat, w, shape, hidden: int = HIDDEN):
-    """loss = mean((b + NN(u) - y)^2) and its gradient in w."""
+    """loss = mean_s (1 - <p_s, y_s>^2 / (<p_s, p_s> <y_s, y_s>)), p = b + NN(u),
+    and its gradient in the weights."""
     out, acts = forward(u, vhat, w, shape, hidden, cache=True)
-    e = b + out - y
-    N = e.size
-    return float(np.sum(e * e) / N), backward(acts, 2.0 * e / N, w, shape, hidden)
+    p = b + out
+    S = p.shape[0]
+    al = np.sum(p * y, axis=1)
+    be = np.sum(p * p, axis=1)
+    ga = np.sum(y * y, axis=1)
+    loss = float(np.mean(1.0 - al * al / (be * ga)))
+    # d/dp of 1 - al^2 / (be ga): -2 al / (be ga) y + 2 al^2 / (be^2 ga) p
+    g = (-2.0 * al / (be * ga))[:, None] * y + (2.0 * al * al / (be * be * ga))[:, None] * p
+    return loss, backward(acts, g / S, w, shape, hidden)
 
 
 @dataclasses.dataclass
@@ -279,7 +294,8 @@ def training_planes(ham, X: np.ndarray, tpa_apply, rtol: float = MINRES_RTOL, ma
     """Training samples from a block X of approximate orbitals.
 
     For each band: e = <x|H|x>, r = H x - e x, s = rms(r), t = the projected
-    correction, base = TPA(r) (``tpa_apply(R) -> W``), c = Re<t|base> / <t|t>;
+    correction, base = TPA(r) (``tpa_apply(R) -> W``),
+    c = sign(Re<t|base>) ||base|| / ||t|| (0 where t = 0);
     returns real planes u = r / s, b = base / s, y = c t / s, stacked as
     [Re of every band; Im of every band], each [2 m][n].
     """
@@ -293,7 +309,10 @@ def training_planes(ham, X: np.ndarray, tpa_apply, rtol: float = MINRES_RTOL, ma
     for i in range(X.shape[0]):
         T[i], _ = correction_target(ham, X[i], e[i], R[i], rtol, maxit)
     tt = np.real(np.sum(T.conj() * T, axis=1))
-    c = np.where(tt > 0.0, np.real(np.sum(T.conj() * base, axis=1)) / np.where(tt > 0.0, tt, 1.0), 0.0)
+    bb = np.real(np.sum(base.conj() * base, axis=1))
+    tb = np.real(np.sum(T.conj() * base, axis=1))
+    sgn = np.where(tb < 0.0, -1.0, 1.0)
+    c = np.where(tt > 0.0, sgn * np.sqrt(bb / np.where(tt > 0.0, tt, 1.0)), 0.0)
     safe = np.where(s > 0.0, s, 1.0)[:, None]
     U, B, Y = R / safe, base / safe, c[:, None] * T / safe
     return (np.concatenate([U.real, U.imag]), np.concatenate([B.real, B.imag]),

@@ -272,7 +272,8 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     w.gram_part_elems = (size_t)16 * 2 * k * k;
     RS_TRY(dev_alloc(ctx, (void **)&w.gram_part, w.gram_part_elems * sizeof(double2)));
     RS_TRY(dev_alloc(ctx, (void **)&w.tau, k * sizeof(double2)));
-    RS_TRY(dev_alloc(ctx, (void **)&w.wv, 2 * k * sizeof(double2)));
+    // the cooperative tridiagonalisation keeps w in two buffers of up to 4 parts
+    RS_TRY(dev_alloc(ctx, (void **)&w.wv, 8 * k * sizeof(double2)));
     for (double **b : {&w.d, &w.e, &w.lam})
         RS_TRY(dev_alloc(ctx, (void **)b, k * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.zt, k * k * sizeof(double)));

@@ -32,7 +32,8 @@ constexpr int GSTAGES = 3;
 constexpr int GTILE = BM * GK * 2;   // 8 KB per operand tile
 constexpr int GSTAGE_BYTES = 8 * GTILE;                  // A re/im hi/lo, B re/im hi/lo
 constexpr int GSMEM = GSTAGES * GSTAGE_BYTES + 1024;     // + alignment slack
-constexpr int GTHREADS = 128;
+constexpr int GTHREADS = 192;        // warp 0: TMA, warp 1: MMA, warps 2-5: accumulator drain
+constexpr int PROMOTE_KB = 32;       // k-blocks per tensor-core accumulation chunk
 constexpr int PLANE_ALIGN = 64;      // plane length granularity (points)
 constexpr long long WAIT_LIMIT = 4000000000LL;          // SM cycles (~2 s) per wait
 
@@ -178,6 +179,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Store 32 consecutive FP32 columns of this thread's TMEM lane (waits for completion).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // Split FP32 complex rows into planar BF16 hi/lo rows [Re | Im], each plane ldh
 // points long (ldh a multiple of 64, points n..ldh-1 zero).  Destination rows
 // dst_row0 + r, row length 2 ldh.  Two points per thread (bf16x2 stores).
@@ -210,12 +232,17 @@ __global__ void k_split_planar(RowBlocksT<float2> src, int nrows, long long n, i
 }
 
 // part[split][M][N] (complex, FP32) = the split's point range of conj(A) B^T from
-// planar split rows.  Grid (N tiles, M tiles, splits), 128 threads, two 128 x 128
-// FP32 accumulators in TMEM (real part in columns 0..127, imaginary part in
-// 128..255).  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, all four warps
-// read the accumulators (warp w owns TMEM lanes 32w..32w+31).  tpb > 0: B is a
-// stack of blocks of blk_rows rows, each Hermitian against A; blockIdx.x = block *
-// tpb + tile in the block, and tiles below the diagonal are skipped.
+// planar split rows.  Grid (N tiles, M tiles, splits), 192 threads: warp 0 lane 0
+// issues TMA, warp 1 lane 0 issues MMAs, warps 2-5 drain the accumulator (warp w
+// owns TMEM lanes 32 (w mod 4) ..).  The MMAs accumulate at most PROMOTE_KB
+// k-blocks in TMEM (columns 0..255: real part 0..127, imaginary part 128..255);
+// the drain warps then add that chunk to a running sum kept in TMEM columns
+// 256..511 with round-to-nearest FP32 adds, and the MMAs of the next chunk start
+// afresh.  The tensor cores' FP32 accumulation loses a little on every step, so
+// an error proportional to the chain length would otherwise grow with the
+// k-blocks per split.  tpb > 0: B is a stack of blocks of blk_rows rows, each
+// Hermitian against A; blockIdx.x = block * tpb + tile in the block, and tiles
+// below the diagonal are skipped.
 __global__ void __launch_bounds__(GTHREADS, 1)
 k_gram_pl(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
           const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int N,
@@ -237,24 +264,29 @@ k_gram_pl(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[GSTAGES];
     __shared__ __align__(8) uint64_t empty_bar[GSTAGES];
+    __shared__ __align__(8) uint64_t acc_full;
+    __shared__ __align__(8) uint64_t acc_empty;
     __shared__ __align__(8) uint64_t acc_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
     const int tm = blockIdx.y, split = blockIdx.z;
     const int kb0 = split * kb_per_split;
     const int nkb = max(0, min(kb_total, kb0 + kb_per_split) - kb0);
+    const int nch = (nkb + PROMOTE_KB - 1) / PROMOTE_KB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < GSTAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 4);   // one arrive per drain warp
         mbar_init(&acc_bar, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&tmem_base, 2 * BN);
+    if (warp == 0) tmem_alloc(&tmem_base, 4 * BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -290,72 +322,123 @@ k_gram_pl(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
+        // ---- MMA issuer: chunk c starts once chunk c - 1 has been drained
         const uint32_t idesc = idesc_bf16(BM, BN), idesc_neg = idesc | IDESC_NEG_A;
         const uint32_t d_re = tmem, d_im = tmem + BN;
-        for (int it = 0; it < nkb; ++it) {
-            const int s = it % GSTAGES, r = it / GSTAGES;
-            if (!mbar_wait(&full_bar[s], r & 1, abort)) break;
+        bool stop = false;
+        for (int c = 0; c < nch && !stop; ++c) {
+            if (c > 0 && !mbar_wait(&acc_empty, (c - 1) & 1, abort)) break;
             tc_fence_after();
-            unsigned char *st = smem + s * GSTAGE_BYTES;
+            const int it0 = c * PROMOTE_KB, it1 = min(nkb, it0 + PROMOTE_KB);
+            for (int it = it0; it < it1; ++it) {
+                const int s = it % GSTAGES, r = it / GSTAGES;
+                if (!mbar_wait(&full_bar[s], r & 1, abort)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                unsigned char *st = smem + s * GSTAGE_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < GK / 16; ++kk) {
-                const int off = kk * 32;   // 16 bf16 = 32 bytes along the 64-byte row
-                const uint64_t arh = smem_desc_k64(st + 0 * GTILE + off), arl = smem_desc_k64(st + 1 * GTILE + off);
-                const uint64_t aih = smem_desc_k64(st + 2 * GTILE + off), ail = smem_desc_k64(st + 3 * GTILE + off);
-                const uint64_t brh = smem_desc_k64(st + 4 * GTILE + off), brl = smem_desc_k64(st + 5 * GTILE + off);
-                const uint64_t bih = smem_desc_k64(st + 6 * GTILE + off), bil = smem_desc_k64(st + 7 * GTILE + off);
-                const uint32_t first = (it | kk) != 0 ? 1u : 0u;
-                // Re += A_re B_re + A_im B_im
-                mma_bf16(d_re, arh, brh, idesc, first);
-                mma_bf16(d_re, arh, brl, idesc, 1u);
-                mma_bf16(d_re, arl, brh, idesc, 1u);
-                mma_bf16(d_re, aih, bih, idesc, 1u);
-                mma_bf16(d_re, aih, bil, idesc, 1u);
-                mma_bf16(d_re, ail, bih, idesc, 1u);
-                // Im += A_re B_im - A_im B_re
-                mma_bf16(d_im, arh, bih, idesc, first);
-                mma_bf16(d_im, arh, bil, idesc, 1u);
-                mma_bf16(d_im, arl, bih, idesc, 1u);
-                mma_bf16(d_im, aih, brh, idesc_neg, 1u);
-                mma_bf16(d_im, aih, brl, idesc_neg, 1u);
-                mma_bf16(d_im, ail, brh, idesc_neg, 1u);
+                for (int kk = 0; kk < GK / 16; ++kk) {
+                    const int off = kk * 32;   // 16 bf16 = 32 bytes along the 64-byte row
+                    const uint64_t arh = smem_desc_k64(st + 0 * GTILE + off), arl = smem_desc_k64(st + 1 * GTILE + off);
+                    const uint64_t aih = smem_desc_k64(st + 2 * GTILE + off), ail = smem_desc_k64(st + 3 * GTILE + off);
+                    const uint64_t brh = smem_desc_k64(st + 4 * GTILE + off), brl = smem_desc_k64(st + 5 * GTILE + off);
+                    const uint64_t bih = smem_desc_k64(st + 6 * GTILE + off), bil = smem_desc_k64(st + 7 * GTILE + off);
+                    const uint32_t acc = (it != it0 || kk != 0) ? 1u : 0u;
+                    // Re += A_re B_re + A_im B_im
+                    mma_bf16(d_re, arh, brh, idesc, acc);
+                    mma_bf16(d_re, arh, brl, idesc, 1u);
+                    mma_bf16(d_re, arl, brh, idesc, 1u);
+                    mma_bf16(d_re, aih, bih, idesc, 1u);
+                    mma_bf16(d_re, aih, bil, idesc, 1u);
+                    mma_bf16(d_re, ail, bih, idesc, 1u);
+                    // Im += A_re B_im - A_im B_re
+                    mma_bf16(d_im, arh, bih, idesc, acc);
+                    mma_bf16(d_im, arh, bil, idesc, 1u);
+                    mma_bf16(d_im, arl, bih, idesc, 1u);
+                    mma_bf16(d_im, aih, brh, idesc_neg, 1u);
+                    mma_bf16(d_im, aih, brl, idesc_neg, 1u);
+                    mma_bf16(d_im, ail, brh, idesc_neg, 1u);
+                }
+                mma_commit(&empty_bar[s]);
             }
-            mma_commit(&empty_bar[s]);
+            if (!stop) mma_commit(&acc_full);   // arrives when the chunk's MMAs are done
         }
         mma_commit(&acc_bar);   // arrives once every MMA issued above has completed
-    }
-    __syncwarp();
-    // ---- epilogue: wait for the accumulators (time-bounded even after an abort,
-    // since TMEM may only be released once the MMAs are done)
-    bool ready = true;
-    {
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&acc_bar, 0)) {
-            if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; ready = false; break; }
+    } else if (warp >= 2) {
+        // ---- drain: running sum (TMEM columns 256..511) += chunk; the last chunk
+        // goes with the sum to this split's partial
+        const int q = warp & 3;   // TMEM lane quarter
+        const int row = tm * BM + q * 32 + lane;
+        float2 *dst_row = part + ((size_t)split * M + row) * N + (size_t)ncol0;
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        const uint32_t acc = tmem + lanes, sum = tmem + lanes + (uint32_t)(2 * BN);
+        for (int c = 0; c < nch; ++c) {
+            // warp-uniform bounded wait (the TMEM loads below are warp-collective)
+            bool ok = true;
+            const long long t0 = clock64();
+            while (true) {
+                const bool done = mbar_try_wait(&acc_full, c & 1);
+                if (__all_sync(0xffffffffu, done)) break;
+                if (__any_sync(0xffffffffu, *abort || clock64() - t0 > WAIT_LIMIT)) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const bool last = c == nch - 1;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                float vr[32], vi[32];
+                tmem_ld32(acc + (uint32_t)c0, vr);
+                tmem_ld32(acc + (uint32_t)(BN + c0), vi);
+                if (c > 0) {
+                    float sr[32], si[32];
+                    tmem_ld32(sum + (uint32_t)c0, sr);
+                    tmem_ld32(sum + (uint32_t)(BN + c0), si);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        vr[i] += sr[i];
+                        vi[i] += si[i];
+                    }
+                }
+                if (!last) {
+                    tmem_st32(sum + (uint32_t)c0, vr);
+                    tmem_st32(sum + (uint32_t)(BN + c0), vi);
+                } else if (row < M && !*abort) {
+                    float2 *dst = dst_row + c0;
+                    const int cmax = min(32, nvalid - c0);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < cmax) dst[i] = make_float2(vr[i], vi[i]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty);
         }
     }
-    tc_fence_after();
-    const bool write = ready && nkb > 0 && !*abort;
-    const int row = tm * BM + warp * 32 + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-        float vr[32], vi[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, vr);
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + c0), vi);
-        if (write && row < M) {
-            float2 *dst = part + ((size_t)split * M + row) * N + (size_t)ncol0 + c0;
-            const int cmax = min(32, nvalid - c0);
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (i < cmax) dst[i] = make_float2(vr[i], vi[i]);
+    __syncwarp();
+    // TMEM is released only once every MMA issued has completed (time-bounded)
+    if (warp == 0) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&acc_bar, 0)) {
+            if (clock64() - t0 > WAIT_LIMIT) {
+                *abort = 1;
+                break;
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, 4 * BN);
     }
     if (threadIdx.x == 0 && *abort) atomicExch(err, 1);
 }
@@ -1044,6 +1127,17 @@ extern "C" rsdft_status rsdft_gram_bf16x3(rsdft_ctx *ctx, const void *a_dev, int
     RowBlocksT<float2> A{{(const float2 *)a_dev, nullptr, nullptr}, {na, 0, 0}};
     RowBlocksT<float2> B{{(const float2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
     return gram_tc(ctx, A, B, (double2 *)g_dev, nb, as_stream(stream));
+}
+
+extern "C" rsdft_status rsdft_gram_sh_bf16x3(rsdft_ctx *ctx, const void *y_dev, const void *hy_dev, int k,
+                                             void *gs_dev, void *gh_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (k < 0 || (k > 0 && (!y_dev || !hy_dev || !gs_dev || !gh_dev)))
+        return fail(ctx, RSDFT_E_INVALID, "bad gram arguments");
+    RS_TRY(ensure_workspace(ctx, 1));
+    RowBlocksT<float2> Y{{(const float2 *)y_dev, nullptr, nullptr}, {k, 0, 0}};
+    RowBlocksT<float2> HY{{(const float2 *)hy_dev, nullptr, nullptr}, {k, 0, 0}};
+    return gram_tc_sh(ctx, Y, HY, (double2 *)gs_dev, (double2 *)gh_dev, k, as_stream(stream));
 }
 
 extern "C" rsdft_status rsdft_rotate_bf16x3(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,

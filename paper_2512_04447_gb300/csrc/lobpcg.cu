@@ -475,12 +475,19 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         // ---- preconditioned residuals W (compact over the active bands)
         const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
         const dim3 scalegrid(std::max(1, std::min(cdiv(n, 256 * 8), 256)), na);   // >= 8 points per thread
-        if (o.precond == RSDFT_PRECOND_TPA) {
+        if (o.precond == RSDFT_PRECOND_TPA || o.precond == RSDFT_PRECOND_LEARNED) {
             RS_TRY(Ops<V>::project(ctx, X, proj, m, st));
             k_tkin<V><<<cdiv(na, 128), 128, 0, st>>>(w.theta, w.vexp, proj, ctx->pt, w.act, na, w.tkin);
             count_launch(ctx);
             RS_LAUNCHED(ctx, "k_tkin");
             RS_TRY(Ops<V>::tpa(ctx, HX, X, w.theta, w.act, w.tkin, T1, W, na, st));
+            if (o.precond == RSDFT_PRECOND_LEARNED) {
+                // W += s_b NN(R_b / s_b); the TPA's FFT scratch holds the residuals
+                k_residual_rows<V><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, T1);
+                count_launch(ctx);
+                RS_LAUNCHED(ctx, "k_residual_rows");
+                RS_TRY(learned_correction<V>(ctx, T1, na, W, st));
+            }
         } else {
             k_residual_rows<V><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, W);
             count_launch(ctx);
@@ -649,8 +656,10 @@ rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lo
         return fail(ctx, RSDFT_E_INVALID, "bad LOBPCG options");
     if (o.precision != RSDFT_FP64 && o.precision != RSDFT_MIXED)
         return fail(ctx, RSDFT_E_INVALID, "unknown precision");
-    if (o.precond != RSDFT_PRECOND_TPA && o.precond != RSDFT_PRECOND_NONE)
+    if (o.precond != RSDFT_PRECOND_TPA && o.precond != RSDFT_PRECOND_NONE && o.precond != RSDFT_PRECOND_LEARNED)
         return fail(ctx, RSDFT_E_INVALID, "unknown preconditioner");
+    if (o.precond == RSDFT_PRECOND_LEARNED && !ctx->nn.ready)
+        return fail(ctx, RSDFT_E_INVALID, "learned preconditioner: no weights set");
     if (stats) *stats = rsdft_lobpcg_stats{};
     return lobpcg_run(ctx, (double2 *)x_dev, nband, o, eig_host, resnorm_host, stats, as_stream(stream));
 }

@@ -101,6 +101,18 @@ struct ScfWork {
     double2 *cbuf = nullptr;                         // [n] complex scratch (FFT)
 };
 
+// Learned preconditioner: weights, Adam state and scratch (precond_nn.cu).
+struct NnState {
+    int ready = 0;                   // weights set
+    float *w = nullptr, *wt = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // [RSDFT_NN_WEIGHTS] each
+    float *vhat = nullptr;           // [n] standardised potential
+    double *dred = nullptr;          // reduction scratch
+    float *act = nullptr;  size_t act_cap = 0;     // inference activations
+    float *part = nullptr; size_t part_cap = 0;    // weight-gradient partials
+    float *bs = nullptr;   size_t bs_cap = 0;      // band scales
+    float *tr = nullptr;   size_t tr_cap = 0;      // training activations and gradients
+};
+
 struct Profiler {
     bool on = false;
     struct Rec { cudaEvent_t a, b; int id; double flops, bytes; };
@@ -129,6 +141,7 @@ struct rsdft_ctx {
     rsdft::Workspace ws;
     rsdft::ScfWork scf;
     rsdft::Profiler prof;
+    rsdft::NnState nn;
     long long launches = 0;          // every kernel launched on this context
     long long coop_fallbacks = 0;    // tridiagonalisations that could not launch cooperatively
     int coop_last_error = 0;         // cudaError_t of the last such launch
@@ -271,5 +284,10 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
 
 // ---- small vector kernels (lobpcg.cu / scf.cu) ----------------------------------
 rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st);
+
+// W[b] += s_b NN(R_b / s_b) (the learned preconditioner's correction) for the
+// nb compact rows of R; requires weights (RSDFT_E_INVALID otherwise).
+template <typename V>
+rsdft_status learned_correction(rsdft_ctx *ctx, const V *R, int nb, V *W, cudaStream_t st);
 
 }  // namespace rsdft

@@ -22,7 +22,9 @@ HEADER = os.path.join(HERE, "..", "include", "rsdft.h")
 OK, E_INVALID, E_GRID_NOT_5SMOOTH, E_OOM, E_CUDA, E_NOT_SPD, E_NUMERIC, E_TIMEOUT, \
     E_NOT_CONVERGED = range(9)
 FP64, MIXED = 0, 1
-PRECOND_NONE, PRECOND_TPA = 0, 1
+PRECOND_NONE, PRECOND_TPA, PRECOND_LEARNED = 0, 1, 2
+NN_HIDDEN = 8
+NN_WEIGHTS = 27 * (2 * NN_HIDDEN + 2 * NN_HIDDEN * NN_HIDDEN + NN_HIDDEN)
 STATUS_NAMES = ["OK", "E_INVALID", "E_GRID_NOT_5SMOOTH", "E_OOM", "E_CUDA", "E_NOT_SPD",
                 "E_NUMERIC", "E_TIMEOUT", "E_NOT_CONVERGED"]
 
@@ -96,6 +98,7 @@ _PROTOS = {
     "rsdft_gram": (ip, [vp, vp, ip, vp, ip, vp, vp]),
     "rsdft_gram_static": (ip, [vp, ip, vp, ip, C.c_longlong, dp, vp, vp]),
     "rsdft_gram_bf16x3": (ip, [vp, vp, ip, vp, ip, vp, vp]),
+    "rsdft_gram_sh_bf16x3": (ip, [vp, vp, vp, ip, vp, vp, vp]),
     "rsdft_rotate_bf16x3": (ip, [vp, vp, ip, vp, ip, vp, vp, vp]),
     "rsdft_rotate": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_rayleigh_ritz": (ip, [vp, vp, vp, ip, ip, dp, vp, vp, vp, vp]),
@@ -116,6 +119,12 @@ _PROTOS = {
     "rsdft_profile_enable": (ip, [vp, ip]),
     "rsdft_profile_read": (ip, [vp, ip, vp, vp, vp, vp]),
     "rsdft_launch_count": (C.c_longlong, [vp]),
+    "rsdft_set_precond_weights": (ip, [vp, vp, C.c_longlong]),
+    "rsdft_get_precond_weights": (ip, [vp, vp, C.c_longlong]),
+    "rsdft_precond_learned": (ip, [vp, vp, vp, vp, ip, vp]),
+    "rsdft_precond_samples": (ip, [vp, vp, ip, dp, ip, vp, vp, vp, vp, vp]),
+    "rsdft_precond_loss_grad": (ip, [vp, vp, vp, vp, ip, vp, vp, vp]),
+    "rsdft_precond_train": (ip, [vp, vp, vp, vp, C.c_longlong, ip, ip, C.c_float, vp, vp]),
 }
 
 K_GRAM, K_ROTATE, K_FFT_XY_FWD, K_FFT_Z, K_FFT_XY_INV, K_PROJECT, K_DENSE, K_GRAM_TC = range(8)
@@ -297,6 +306,39 @@ class Context:
         self._check(lib().rsdft_precondition_tpa(self._h, _ptr(r), _ptr(w), _ptr(tkin), r.shape[0],
                                                  _stream()))
 
+    # ---- learned preconditioner
+    def set_precond_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(lib().rsdft_set_precond_weights(self._h, _ptr(w), w.size))
+
+    def get_precond_weights(self) -> np.ndarray:
+        w = np.zeros(NN_WEIGHTS, dtype=np.float32)
+        self._check(lib().rsdft_get_precond_weights(self._h, _ptr(w), w.size))
+        return w
+
+    def precond_learned(self, r, base, w):
+        self._check(lib().rsdft_precond_learned(self._h, _ptr(r), _ptr(base), _ptr(w), r.shape[0], _stream()))
+
+    def precond_samples(self, x, u, b, y, rtol=1e-3, maxit=500) -> np.ndarray:
+        """Training planes u, b, y ([2 nband][n] float32 device tensors); returns MINRES iterations."""
+        it = np.zeros(x.shape[0], dtype=np.int32)
+        self._check(lib().rsdft_precond_samples(self._h, _ptr(x), x.shape[0], rtol, maxit, _ptr(u), _ptr(b),
+                                                _ptr(y), _ptr(it), _stream()))
+        return it
+
+    def precond_loss_grad(self, u, b, y):
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.zeros(NN_WEIGHTS, dtype=np.float32)
+        self._check(lib().rsdft_precond_loss_grad(self._h, _ptr(u), _ptr(b), _ptr(y), u.shape[0], _ptr(loss),
+                                                  _ptr(grad), _stream()))
+        return float(loss[0]), grad
+
+    def precond_train(self, u, b, y, steps, batch, lr) -> np.ndarray:
+        loss = np.zeros(steps, dtype=np.float32)
+        self._check(lib().rsdft_precond_train(self._h, _ptr(u), _ptr(b), _ptr(y), u.shape[0], steps, batch,
+                                              lr, _ptr(loss), _stream()))
+        return loss
+
     # ---- subspace pieces
     def gram(self, a, b, g):
         self._check(lib().rsdft_gram(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(g),
@@ -308,6 +350,10 @@ class Context:
     def gram_bf16x3(self, a, b, g):
         self._check(lib().rsdft_gram_bf16x3(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0],
                                             _ptr(g), _stream()))
+
+    def gram_sh_bf16x3(self, y, hy, gs, gh):
+        self._check(lib().rsdft_gram_sh_bf16x3(self._h, _ptr(y), _ptr(hy), y.shape[0], _ptr(gs), _ptr(gh),
+                                               _stream()))
 
     def rotate_bf16x3(self, y, c, out0, out1):
         """rsdft_rotate_bf16x3: out1 = C[m:]^T Y[m:], out0 = C[:m]^T Y[:m] + out1."""

@@ -37,6 +37,29 @@ def test_gram_bf16x3_matches_fp64(N, na, nb):
     assert err < BF16X3_TOL
 
 
+@pytest.mark.parametrize("N,k", [((24, 24, 24), 16), ((24, 24, 24), 144), ((20, 18, 15), 200),
+                                 ((24, 24, 24), 288), ((24, 24, 24), 432), ((64, 64, 64), 144)])
+def test_gram_sh_bf16x3_hermitian_pair(N, k):
+    """G_S = <Y|Y> and G_H = <Y|HY> from one GEMM against [Y; HY] (the
+    Rayleigh-Ritz pair; several row tiles, many K splits on the 64^3 grid)."""
+    ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
+    y = draw_x0(5, k, ctx.n).astype(np.complex64)
+    # a Hermitian operator on the grid (a real potential), so that <Y|HY> is Hermitian
+    vr = np.random.default_rng(6).uniform(-2.0, 1.0, ctx.n)
+    hy = (vr[None, :] * y.astype(np.complex128)).astype(np.complex64)
+    gs = torch.full((k, k), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+    gh = torch.full((k, k), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+    ctx.gram_sh_bf16x3(dev(y), dev(hy), gs, gh)
+    Y64, HY64 = y.astype(np.complex128), hy.astype(np.complex128)
+    rs, rh = inner(Y64, Y64, ctx.dV), inner(Y64, HY64, ctx.dV)
+    rh = 0.5 * (rh + rh.conj().T)
+    GS, GH = host(gs), host(gh)
+    es, eh = rel_err(GS, rs), rel_err(GH, rh)
+    print(f"split-BF16 Hermitian pair k={k} on {ctx.n} points: {es:.2e} (S), {eh:.2e} (H)")
+    assert es < BF16X3_TOL and eh < BF16X3_TOL
+    assert np.array_equal(GS, GS.conj().T) and np.array_equal(GH, GH.conj().T)
+
+
 def test_gram_bf16x3_two_calls_in_a_row_and_hermitian_block():
     N = (24, 24, 24)
     ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))

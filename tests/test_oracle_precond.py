@@ -119,6 +119,27 @@ def test_first_adam_step_is_lr_sign_g():
     assert np.allclose(w1 - w, -0.01 * np.sign(g), atol=1e-7, rtol=0)
 
 
+def test_loss_is_one_minus_cos_squared_and_scale_free():
+    r = _rng(11)
+    hidden = 3
+    w = r.standard_normal(P.weight_count(hidden)) * 0.3
+    vhat = P.standardise(r.standard_normal(N))
+    u = r.standard_normal((3, N))
+    b = r.standard_normal((3, N))
+    y = r.standard_normal((3, N))
+    L, _ = P.loss_and_grad(u, b, y, vhat, w, SHAPE, hidden)
+    pv = b + P.forward(u, vhat, w, SHAPE, hidden)
+    cos = [np.dot(pv[i], y[i]) / (np.linalg.norm(pv[i]) * np.linalg.norm(y[i])) for i in range(3)]
+    assert abs(L - np.mean([1.0 - c * c for c in cos])) < 1e-14
+    # the target's scale and sign do not matter
+    L2, _ = P.loss_and_grad(u, b, -3.0 * y, vhat, w, SHAPE, hidden)
+    assert abs(L - L2) < 1e-14
+    # a prediction along the target has zero loss
+    w0 = draw_nn_weights(0, hidden)
+    L0, g0 = P.loss_and_grad(u, b, 2.5 * b, vhat, w0, SHAPE, hidden)
+    assert abs(L0) < 1e-14
+
+
 def test_training_reduces_the_loss_on_a_learnable_map():
     # targets made by a fixed network: a network of the same shape can fit them
     r = _rng(8)
@@ -185,11 +206,17 @@ def test_training_planes_and_learned_apply():
     assert U.shape == B.shape == Y.shape == (8, g.n)
     # u has unit complex rms per band: Re and Im planes together
     assert np.allclose(np.sum(U[:4] ** 2 + U[4:] ** 2, axis=1) / g.n, 1.0, atol=1e-12)
-    # the scaled target matches TPA at least as well as any multiple of t: c is the projection
+    # the target is t rescaled to the TPA norm, pointing along TPA, and a multiple of t
     Bc, Yc = B[:4] + 1j * B[4:], Y[:4] + 1j * Y[4:]
+    HXa = ham.apply(X)
+    ea = np.real(np.sum(X.conj() * HXa, axis=1)) * g.dV
+    Ra = HXa - ea[:, None] * X
     for i in range(4):
-        resid = Bc[i] - Yc[i]
-        assert abs(np.real(np.vdot(Yc[i], resid))) < 1e-9 * np.linalg.norm(Yc[i]) * np.linalg.norm(Bc[i])
+        assert abs(np.linalg.norm(Yc[i]) - np.linalg.norm(Bc[i])) <= 1e-12 * np.linalg.norm(Bc[i])
+        assert np.real(np.vdot(Yc[i], Bc[i])) >= 0.0
+        t, _ = P.correction_target(ham, X[i], ea[i], Ra[i], maxit=300)
+        cosang = abs(np.vdot(t, Yc[i])) / (np.linalg.norm(t) * np.linalg.norm(Yc[i]))
+        assert abs(cosang - 1.0) < 1e-12
     # learned_apply with zero weights is the TPA base itself
     HX = ham.apply(X)
     e = np.real(np.sum(X.conj() * HX, axis=1)) * g.dV
