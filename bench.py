@@ -582,7 +582,7 @@ def train_learned(R, torch, wl_train, seeds, snapshots, steps, batch, lr, rtol=1
     return w, info
 
 
-def holdout_loss(R, torch, wl, w, nb=16, k=2):
+def holdout_loss(R, torch, wl, w, nb=16, k=12):
     """Loss of TPA alone and of TPA + the trained network on samples the network
     never saw: the first nb bands of the judged cell after k FP64 LOBPCG
     iterations from its seeded start (targets by MINRES, 400 iterations at most)."""
@@ -649,7 +649,7 @@ def run_learned(args):
     result = {}
     for c in pick:
         tr, ev = chems[c]
-        w, info = train_learned(R, torch, workloads.REGISTRY[tr](), seeds=range(4), snapshots=(1, 2, 4, 8, 16),
+        w, info = train_learned(R, torch, workloads.REGISTRY[tr](), seeds=range(4), snapshots=(8, 12, 16, 20, 24),
                                 steps=args.train_steps, batch=args.train_batch, lr=args.train_lr)
         wl = workloads.REGISTRY[ev]()
         holdout = holdout_loss(R, torch, wl, w)

@@ -26,6 +26,22 @@ __device__ __forceinline__ double2 c_mulc(double2 a, double2 b) {  // a * conj(b
 }
 __device__ __forceinline__ double2 c_conj(double2 a) { return make_double2(a.x, -a.y); }
 
+// 1/x in FP64 by the Newton-Raphson iteration y <- y + y (1 - x y) from an FP32
+// seed: each step squares the relative error (2^-23 -> 2^-46 -> below one ulp),
+// two FMA pairs instead of the long FP64 division sequence.  Arguments outside
+// the FP32 range take the division.
+__device__ __forceinline__ double rcp_nr(double x) {
+    const float xf = (float)x;
+    const float ax = fabsf(xf);
+    if (!(ax > 1e-30f && ax < 1e30f)) return 1.0 / x;
+    double y = (double)__frcp_rn(xf);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+
 // Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); the warp
 // partials are combined by warp 0 with shuffles (a chain of dependent FP64 adds
 // in one thread costs ~64 cycles per add on this part).
@@ -83,7 +99,7 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
             const int dr = !(d > floor_);
             s_drop[c] = dr;
             s_l[c] = dr ? 1.0 : sqrt(d);
-            s_il[c] = dr ? 1.0 : 1.0 / s_l[c];
+            s_il[c] = dr ? 1.0 : rcp_nr(s_l[c]);
             sD[c][c] = make_double2(s_l[c], 0.0);
         }
         __syncthreads();
@@ -572,10 +588,10 @@ __device__ void house_inplace(double2 *x, int L, double2 &tau, double &beta, dou
             b = alpha.x;
         } else {
             b = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2), alpha.x);
-            const double ib = 1.0 / b;
+            const double ib = rcp_nr(b);
             t = make_double2((b - alpha.x) * ib, -alpha.y * ib);
             const double2 den = make_double2(alpha.x - b, alpha.y);
-            const double idd = 1.0 / (den.x * den.x + den.y * den.y);
+            const double idd = rcp_nr(den.x * den.x + den.y * den.y);
             scal = make_double2(den.x * idd, -den.y * idd);
         }
         sh[0] = t.x;
@@ -590,6 +606,15 @@ __device__ void house_inplace(double2 *x, int L, double2 &tau, double &beta, dou
     const double2 scal = make_double2(sh[3], sh[4]);
     for (int r = threadIdx.x; r < L; r += blockDim.x) x[r] = r == 0 ? make_double2(1.0, 0.0) : c_mul(x[r], scal);
     __syncthreads();
+}
+
+// Column segments per row of the fused update + matvec of one step: enough items
+// for one per SM sub-partition (4 nb) when rows are few, at least 32 columns each.
+constexpr int TRI_PARTS = 4;
+__device__ __forceinline__ int tri_parts(int rows, int nb) {
+    const int by_warps = rows > 0 ? (4 * nb) / rows : 1;
+    const int by_cols = rows / 32;
+    return max(1, min(TRI_PARTS, min(by_warps, by_cols)));
 }
 
 __global__ void __launch_bounds__(256)
@@ -638,28 +663,40 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
         if (lane == 0) wbuf[r - 1] = c_mul(ti, make_double2(sx, sy));
     }
     if (!grid_sync(gs, nb, limit, &s_ok, epoch)) return;
+    int pw = 1;   // parts the current w is split into (summed on reading)
     for (int i = 0; i < k - 1; ++i) {
         L = k - i - 1;
-        const double2 *w = wbuf + (i & 1) * k;
-        double2 *wn = wbuf + ((i + 1) & 1) * k;
+        const double2 *w = wbuf + (size_t)(i & 1) * TRI_PARTS * k;
+        double2 *wn = wbuf + (size_t)((i + 1) & 1) * TRI_PARTS * k;
         // w' = w + alpha v, alpha = -1/2 tau (w^H v); the raw column i+1 is
         // fetched in the same sweep
+        // (every FP64 instruction costs the same whether or not it fuses, so the
+        // redundant per-block loops below are written as FMA chains)
         double2 acc = make_double2(0.0, 0.0);
         for (int r = threadIdx.x; r < L; r += blockDim.x) {
-            const double2 wr = ldcg2(w + r);
+            double2 wr = ldcg2(w + r);
+            for (int p = 1; p < pw; ++p) {
+                const double2 q = ldcg2(w + (size_t)p * k + r);
+                wr.x += q.x;
+                wr.y += q.y;
+            }
+            const double2 vr = sv[r];
             sw[r] = wr;
-            const double2 p = c_mul(c_conj(wr), sv[r]);
-            acc.x += p.x;
-            acc.y += p.y;
+            acc.x = fma(wr.x, vr.x, acc.x);        // conj(w) v
+            acc.x = fma(wr.y, vr.y, acc.x);
+            acc.y = fma(wr.x, vr.y, acc.y);
+            acc.y = fma(-wr.y, vr.x, acc.y);
             if (r >= 1) sn[r - 1] = ldcg2(a + (size_t)(i + 1 + r) * ld + (i + 1));
         }
         acc = block_sum_c(acc, sh2);
         const double2 tw = c_mul(ti, acc);
         const double2 alpha = make_double2(-0.5 * tw.x, -0.5 * tw.y);
         for (int r = threadIdx.x; r < L; r += blockDim.x) {
-            const double2 p = c_mul(alpha, sv[r]);
-            sw[r].x += p.x;
-            sw[r].y += p.y;
+            const double2 vr = sv[r];
+            double2 x = sw[r];
+            x.x = fma(alpha.x, vr.x, fma(-alpha.y, vr.y, x.x));
+            x.y = fma(alpha.x, vr.y, fma(alpha.y, vr.x, x.y));
+            sw[r] = x;
         }
         __syncthreads();
         const double dnext = ldcg2(a + (size_t)(i + 1) * ld + (i + 1)).x - 2.0 * sw[0].x;
@@ -669,9 +706,14 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
         }
         // updated column i+1 below the diagonal -> reflector i+1
         const int Ln = L - 1;
+        const double2 w0 = sw[0];
         for (int q = threadIdx.x; q < Ln; q += blockDim.x) {
-            const double2 p = c_mulc(sv[q + 1], sw[0]), pw = sw[q + 1];
-            sn[q] = make_double2(sn[q].x - p.x - pw.x, sn[q].y - p.y - pw.y);
+            // sn - v conj(w'_0) - w'
+            const double2 vq = sv[q + 1], pw = sw[q + 1];
+            double2 x = sn[q];
+            x.x = fma(-vq.y, w0.y, fma(-vq.x, w0.x, x.x - pw.x));
+            x.y = fma(vq.x, w0.y, fma(-vq.y, w0.x, x.y - pw.y));
+            sn[q] = x;
         }
         __syncthreads();
         double2 tn;
@@ -687,15 +729,23 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
         }
         // rows >= i+2: A -= v w'^H + w' v^H on columns >= i+2, fused with
         // w_{i+1} = tau_{i+1} A^(i+1) v_{i+1}
+        // work items (row, column segment): P segments per row when there are few
+        // rows, so that up to one item lands on each SM sub-partition (warps w and
+        // w + 4 of a CTA share one; items fill warp slots 0-3 of every CTA first)
         const int o = i + 1;
-        for (int r = blockIdx.x + nb * wib; r < k; r += nb * nwb) {
-            if (r < i + 2) continue;
+        const int rows = k - i - 2;
+        const int P = tri_parts(rows, nb);
+        const int seg = ((rows + P - 1) / P + 31) & ~31;
+        for (int t = blockIdx.x + nb * wib; t < rows * P; t += nb * nwb) {
+            const int rr = t / P, p = t - rr * P;
+            const int r = i + 2 + rr;
+            const int c0 = i + 2 + p * seg, c1 = min(k, c0 + seg);
             double2 *row = a + (size_t)r * ld;
             const double2 vr = sv[r - o], wr = sw[r - o];
             double sx = 0.0, sy = 0.0;
             // x = a - v_r conj(w_c) - w_r conj(v_c) and the matvec term x s_c as 12
             // FMAs per element (an FP64 instruction costs the same whatever it fuses)
-            for (int c = i + 2 + lane; c < k; c += 32) {
+            for (int c = c0 + lane; c < c1; c += 32) {
                 const double2 xv = ldcg2(row + c);
                 const double2 wc = sw[c - o], vc = sv[c - o], sc = sn[c - i - 2];
                 double xr = fma(-vr.x, wc.x, xv.x);
@@ -716,8 +766,9 @@ k_tridiag_coop(double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau, do
                 sx += __shfl_xor_sync(0xffffffffu, sx, o2);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o2);
             }
-            if (lane == 0) wn[r - i - 2] = c_mul(tn, make_double2(sx, sy));
+            if (lane == 0) wn[(size_t)p * k + rr] = c_mul(tn, make_double2(sx, sy));
         }
+        pw = P;
         if (!grid_sync(gs, nb, limit, &s_ok, epoch)) return;
         double2 *t = sv;
         sv = sn;
@@ -806,34 +857,48 @@ __global__ void k_tri_prep(const double *d, const double *e, int k, double *scr)
     }
 }
 
-// Multisection for the lowest nkeep eigenvalues of T, one warp per eigenvalue
-// j: each round the 32 lanes take Sturm counts at 32 interior points of the
-// bracket [lo, hi] and the bracket shrinks to the sub-interval that holds the
-// j-th eigenvalue (counts are monotone in x, so the lanes with count > j form
-// a suffix).  Stops at a bracket of 4 ulps.
-__global__ void k_bisect(const double *d, int k, int nkeep, const double *scr, double *lam) {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= nkeep) return;   // whole warps exit together (j is uniform per warp)
+// Multisection for the lowest nkeep eigenvalues of T, one 128-thread CTA per
+// eigenvalue j (one warp per SM sub-partition, so the four Sturm chains of a
+// round run side by side): each round the threads take Sturm counts at 128
+// interior points of the bracket [lo, hi] and the bracket shrinks to the
+// sub-interval that holds the j-th eigenvalue (counts are monotone in x, so
+// the points with count > j form a suffix); a round divides the bracket by 129
+// (against 33 with one warp, so about 30% fewer sequential rounds).  Stops at
+// a bracket of 4 ulps.
+constexpr int BIS_T = 128;
+__global__ void __launch_bounds__(BIS_T) k_bisect(const double *d, int k, int nkeep, const double *scr, double *lam) {
+    const int j = blockIdx.x;
+    if (j >= nkeep) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __shared__ unsigned s_ball[BIS_T / 32];
+    __shared__ double s_x[BIS_T];
     const double *e2 = scr + 8;
+    const double step = 1.0 / (double)(BIS_T + 1);
     double lo = scr[1], hi = scr[2];
     for (int round = 0; round < 40; ++round) {
+        // lo and hi are the same in every thread (taken from shared memory)
         if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const double x = lo + (hi - lo) * ((double)(t + 1) * step);
         const int c = sturm_count(d, e2, k, x);
         const unsigned ball = __ballot_sync(0xffffffffu, c > j);
-        const double xprev = __shfl_up_sync(0xffffffffu, x, 1);
-        if (ball == 0u) {
-            lo = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) s_ball[warp] = ball;
+        s_x[t] = x;
+        __syncthreads();
+        int f = -1;
+        for (int w = 0; w < BIS_T / 32; ++w)
+            if (s_ball[w]) {
+                f = w * 32 + __ffs(s_ball[w]) - 1;
+                break;
+            }
+        if (f < 0) {
+            lo = s_x[BIS_T - 1];
         } else {
-            const int f = __ffs(ball) - 1;
-            const double xf = __shfl_sync(0xffffffffu, x, f);
-            const double xl = __shfl_sync(0xffffffffu, xprev, f);
-            if (f > 0) lo = xl;
-            hi = xf;
+            if (f > 0) lo = s_x[f - 1];
+            hi = s_x[f];
         }
+        __syncthreads();
     }
-    if (lane == 0) lam[j] = 0.5 * (lo + hi);
+    if (t == 0) lam[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_uniform(unsigned long long x) {
@@ -876,7 +941,7 @@ k_inverse_iter(const double *d, const double *e, int k, int nkeep, const double 
             const double sub = e[i];
             if (fabs(D[i]) >= fabs(sub)) {
                 if (D[i] == 0.0) D[i] = tiny;
-                M[i] = sub / D[i];
+                M[i] = sub * rcp_nr(D[i]);
                 D[i + 1] -= M[i] * U1[i];
             } else {
                 // interchange rows i and i+1, then eliminate
@@ -1041,9 +1106,12 @@ k_backtransform_reg(int k, const double2 *__restrict__ vh, int ldv, const double
             }
         }
         if (tc.x != 0.0 || tc.y != 0.0) {   // uniform over the block
+            // v_i is zero on rows <= i: register slices q whose rows all lie
+            // there are skipped (the test is the same in every thread)
             double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
             for (int q = 0; q < BT_R; ++q) {   // conj(v) z
+                if ((q + 1) * bd <= i + 1) continue;
                 acc.x = fma(vc[q].x, zr[q].x, acc.x);
                 acc.x = fma(vc[q].y, zr[q].y, acc.x);
                 acc.y = fma(vc[q].x, zr[q].y, acc.y);
@@ -1053,6 +1121,7 @@ k_backtransform_reg(int k, const double2 *__restrict__ vh, int ldv, const double
             const double2 f = c_mul(tc, acc);
 #pragma unroll
             for (int q = 0; q < BT_R; ++q) {   // z -= f v
+                if ((q + 1) * bd <= i + 1) continue;
                 zr[q].x = fma(-f.x, vc[q].x, zr[q].x);
                 zr[q].x = fma(f.y, vc[q].y, zr[q].x);
                 zr[q].y = fma(-f.x, vc[q].y, zr[q].y);
@@ -1149,7 +1218,7 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     count_launch(ctx);
     // one warp per eigenvalue and one CTA per warp: the Sturm counts and the
     // substitutions are FP64 chains, so the eigenvalues spread over the SMs
-    k_bisect<<<nkeep, 32, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+    k_bisect<<<nkeep, BIS_T, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
     count_launch(ctx);
     {
         const size_t ii_smem = (size_t)6 * k * sizeof(double);
