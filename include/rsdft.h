@@ -243,6 +243,9 @@ typedef struct {
                               Gram matrices with split-BF16 tcgen05 GEMMs; 2 does
                               the Ritz rotations that way too (when m <= 240)
                               (default 0)                                         */
+    int learned_iters;     /* RSDFT_PRECOND_LEARNED: add the network correction in
+                              the first learned_iters iterations only, TPA alone
+                              after them; 0 = in every iteration (default 0)      */
 } rsdft_lobpcg_opts;
 
 typedef struct {

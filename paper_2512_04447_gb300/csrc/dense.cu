@@ -25,6 +25,16 @@ __device__ __forceinline__ double2 c_mulc(double2 a, double2 b) {  // a * conj(b
     return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ double2 c_conj(double2 a) { return make_double2(a.x, -a.y); }
+// s += a b and s -= a b as four FMAs each (an FP64 instruction costs the same
+// whether or not it fuses, so complex products are written as FMA chains)
+__device__ __forceinline__ void c_fma(double2 &s, double2 a, double2 b) {
+    s.x = fma(a.x, b.x, fma(-a.y, b.y, s.x));
+    s.y = fma(a.x, b.y, fma(a.y, b.x, s.y));
+}
+__device__ __forceinline__ void c_fms(double2 &s, double2 a, double2 b) {
+    s.x = fma(-a.x, b.x, fma(a.y, b.y, s.x));
+    s.y = fma(-a.x, b.y, fma(-a.y, b.x, s.y));
+}
 
 // 1/x in FP64 by the Newton-Raphson iteration y <- y + y (1 - x y) from an FP32
 // seed: each step squares the relative error (2^-23 -> 2^-46 -> below one ulp),
@@ -119,9 +129,12 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
                 while (ri * (ri + 1) / 2 > t) --ri;
                 while ((ri + 1) * (ri + 2) / 2 <= t) ++ri;
                 const int i = c + 1 + ri, c2 = c + 1 + (t - ri * (ri + 1) / 2);
-                const double2 p = c_mulc(sD[i][c], sD[c2][c]);
-                sD[i][c2].x -= p.x;
-                sD[i][c2].y -= p.y;
+                // -= l_i conj(l_c2), as four FMAs
+                const double2 p = sD[i][c], q = sD[c2][c];
+                double2 x = sD[i][c2];
+                x.x = fma(-p.x, q.x, fma(-p.y, q.y, x.x));
+                x.y = fma(-p.y, q.x, fma(p.x, q.y, x.y));
+                sD[i][c2] = x;
             }
         }
         __syncthreads();
@@ -148,20 +161,24 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
             x.x = __shfl_sync(0xffffffffu, x.x, c);
             x.y = __shfl_sync(0xffffffffu, x.y, c);
             if (lane == c) v = x;
-            else if (lane > c && lane < nb) {
-                const double2 p = c_mulc(x, sD[lane][c]);
-                v.x -= p.x;
-                v.y -= p.y;
+            else if (lane > c && lane < nb) {   // v -= x conj(l_lane,c)
+                const double2 q = sD[lane][c];
+                v.x = fma(-x.x, q.x, fma(-x.y, q.y, v.x));
+                v.y = fma(-x.y, q.x, fma(x.x, q.y, v.y));
             }
         }
         if (lane < nb) row[lane] = v;
     }
 }
 
-// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb;
+// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb,
+// in CHOL_TS x CHOL_TS tiles (16: one entry per thread, and four times the tiles of a
+// 32-tile grid, so the FP64 work spreads over about twice as many SMs);
 // block (0, 0) also stores the panel's factored diagonal block from diag
 // (lower triangle) into a.  Launched with at least one block.
-__global__ void k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restrict__ diag) {
+constexpr int CHOL_TS = 16;
+__global__ void __launch_bounds__(256)
+k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restrict__ diag) {
     if (blockIdx.x == 0 && blockIdx.y == 0) {
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
             const int r = t / nb, c = t % nb;
@@ -172,23 +189,23 @@ __global__ void k_chol_update(double2 *a, int k, int ld, int kb, int nb, const d
     if (t0 >= k) return;
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
-    const int i0 = t0 + ti * 32, j0 = t0 + tj * 32;
-    __shared__ double2 Li[32][NBK + 1], Lj[32][NBK + 1];
-    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+    const int i0 = t0 + ti * CHOL_TS, j0 = t0 + tj * CHOL_TS;
+    __shared__ double2 Li[CHOL_TS][NBK + 1], Lj[CHOL_TS][NBK + 1];
+    for (int t = threadIdx.x; t < CHOL_TS * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
         Li[r][c] = (i0 + r < k) ? a[(size_t)(i0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
         Lj[r][c] = (j0 + r < k) ? a[(size_t)(j0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-        const int r = t / 32, s = t % 32;
+    for (int t = threadIdx.x; t < CHOL_TS * CHOL_TS; t += blockDim.x) {
+        const int r = t / CHOL_TS, s = t % CHOL_TS;
         const int i = i0 + r, j = j0 + s;
         if (i >= k || j >= k || j > i) continue;
         double sx = 0.0, sy = 0.0;
-        for (int c = 0; c < nb; ++c) {
-            const double2 p = c_mulc(Li[r][c], Lj[s][c]);
-            sx += p.x;
-            sy += p.y;
+        for (int c = 0; c < nb; ++c) {   // l_i conj(l_j) as four FMAs
+            const double2 p = Li[r][c], q = Lj[s][c];
+            sx = fma(p.x, q.x, fma(p.y, q.y, sx));
+            sy = fma(p.y, q.x, fma(-p.x, q.y, sy));
         }
         double2 &x = a[(size_t)i * ld + j];
         x.x -= sx;
@@ -257,9 +274,7 @@ __global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb
         x.y = __shfl_sync(0xffffffffu, x.y, c);
         if (lane == c) v = x;
         else if (lane > c && lane < nb) {
-            const double2 p = c_mul(Ls[lane][c], x);
-            v.x -= p.x;
-            v.y -= p.y;
+            c_fms(v, Ls[lane][c], x);
         }
     }
     if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
@@ -286,15 +301,11 @@ k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int kc, int rb, int 
     const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
     const int i = i0 + r, col = c0 + s_;
     if (i >= kc || col >= ncol) return;
-    double sx = 0.0, sy = 0.0;
-    for (int c = 0; c < nb; ++c) {
-        const double2 p = c_mul(Ls[r][c], Xs[c][s_]);
-        sx += p.x;
-        sy += p.y;
-    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < nb; ++c) c_fma(acc, Ls[r][c], Xs[c][s_]);
     double2 &x = b[(size_t)i * ldb + col];
-    x.x -= sx;
-    x.y -= sy;
+    x.x -= acc.x;
+    x.y -= acc.y;
 }
 
 // Backward: solve L^H X = B in place, block rows from the bottom.  Diagonal
@@ -320,9 +331,7 @@ __global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int r
         x.y = __shfl_sync(0xffffffffu, x.y, c);
         if (lane == c) v = x;
         else if (lane < c) {
-            const double2 p = c_mul(c_conj(Ls[c][lane]), x);
-            v.x -= p.x;
-            v.y -= p.y;
+            c_fms(v, c_conj(Ls[c][lane]), x);
         }
     }
     if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
@@ -346,15 +355,11 @@ k_trsm_upperH_update(const double2 *__restrict__ L, int ldl, int rb, int nb, dou
     const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
     const int i = i0 + r, col = c0 + s_;
     if (i >= rb || col >= ncol) return;
-    double sx = 0.0, sy = 0.0;
-    for (int c = 0; c < nb; ++c) {
-        const double2 p = c_mul(Ls[r][c], Xs[c][s_]);
-        sx += p.x;
-        sy += p.y;
-    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < nb; ++c) c_fma(acc, Ls[r][c], Xs[c][s_]);
     double2 &x = b[(size_t)i * ldb + col];
-    x.x -= sx;
-    x.y -= sy;
+    x.x -= acc.x;
+    x.y -= acc.y;
 }
 
 static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
@@ -1289,7 +1294,7 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
                                                                          w.drop, w.Km);
         count_launch(ctx);
         const int rest = k - kb - nb;
-        dim3 g(std::max(1, cdiv(rest, 32)), std::max(1, cdiv(rest, 32)));
+        dim3 g(std::max(1, cdiv(rest, CHOL_TS)), std::max(1, cdiv(rest, CHOL_TS)));
         k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.Km);
         count_launch(ctx);
     }

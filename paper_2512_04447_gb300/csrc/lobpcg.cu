@@ -481,7 +481,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
             count_launch(ctx);
             RS_LAUNCHED(ctx, "k_tkin");
             RS_TRY(Ops<V>::tpa(ctx, HX, X, w.theta, w.act, w.tkin, T1, W, na, st));
-            if (o.precond == RSDFT_PRECOND_LEARNED) {
+            if (o.precond == RSDFT_PRECOND_LEARNED && (o.learned_iters <= 0 || rs.iterations + it < o.learned_iters)) {
                 // W += s_b NN(R_b / s_b); the TPA's FFT scratch holds the residuals
                 k_residual_rows<V><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, T1);
                 count_launch(ctx);
@@ -640,6 +640,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->pivot_tol = 1e-8;
     o->switch_tol = 1e-4;
     o->tensor_cores = 0;
+    o->learned_iters = 0;
 }
 
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,

@@ -51,7 +51,7 @@ class Projectors(C.Structure):
 class LobpcgOpts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("tol", C.c_double), ("nconv", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double),
-                ("switch_tol", C.c_double), ("tensor_cores", C.c_int)]
+                ("switch_tol", C.c_double), ("tensor_cores", C.c_int), ("learned_iters", C.c_int)]
 
 
 class LobpcgStats(C.Structure):
