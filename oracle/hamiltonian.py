@@ -16,7 +16,9 @@ Pins (tests/test_oracle_hamiltonian.py): plane waves are eigenvectors of T with
 eigenvalue |G|^2/2; Hermiticity; V_NL beta = E beta for a lone normalised
 projector; on a 12^3 grid H equals a dense matrix built independently
 (Kronecker sum of explicit cosine-series 1D kinetic matrices + diagonal V +
-brute-force projector outer products).
+brute-force projector outer products); kinetic_energy of a normalised plane
+wave is |G|^2/2 and of an equal mix of two is their mean
+(tests/test_oracle_pins_closed_form.py).
 """
 from __future__ import annotations
 

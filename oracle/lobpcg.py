@@ -35,7 +35,10 @@ Pins (tests/test_oracle_lobpcg.py): free-electron spectrum (2pi/L)^2 |k|^2 / 2
 with closed shells; separable potential = sums of three 1D dense spectra on a
 non-cubic grid; constant-potential shift; 12^3 brute-force dense
 diagonalisation; X^H X dV = I; Ritz values non-increasing (Courant-Fischer);
-rank-1 secular equation of a lone s projector.
+rank-1 secular equation of a lone s projector.  TPA itself
+(tests/test_oracle_pins_closed_form.py): a plane wave maps to K(x_G) times
+itself, with t_b chosen so that K takes the exact rational values 40/41,
+65/81 and 175/431, per G in a sum of plane waves, and t_b < 1e-12 read as 1.
 """
 from __future__ import annotations
 

@@ -52,7 +52,11 @@ theorem through numpy's FFT; the adjoint satisfies <conv a, g> = <a, conv^T g>;
 the network is odd in u; the backward pass matches central finite differences;
 the first Adam step moves every weight by lr sign(g); MINRES equals a dense
 solve on a small indefinite Hermitian system and on the projected system of a
-6^3 Hamiltonian built densely, with monotone residuals.
+6^3 Hamiltonian built densely, with monotone residuals.  learned_apply
+(tests/test_oracle_pins_closed_form.py): with centre-tap weights the network
+is the pointwise map tanh(tanh(tanh(a u + c u vhat))), checked per band with
+its rms scale and Re/Im planes; it commutes with positive and imaginary
+scalings of (r, base).
 """
 from __future__ import annotations
 

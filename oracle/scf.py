@@ -36,7 +36,9 @@ Definitions (orbitals normalised with <psi|psi> = sum |psi|^2 dV = 1):
 Pins (tests/test_oracle_scf.py): sum rho dV = N_e; Hartree of cos(G.r) is
 (4 pi / |G|^2) cos(G.r); eps_x = -0.458165 / r_s; v_xc equals a central finite
 difference of d(rho eps_xc)/d rho; the PZ81 branches meet at r_s = 1 to 4e-5;
-sum f = N_e; kT -> 0 gives aufbau; Anderson depth 0 is linear mixing and keeps
+sum f = N_e; kT -> 0 gives aufbau; the entropy equals -dOmega/dT at fixed mu
+(central difference of the fermion grand potential) and is 2 ln 2 for one
+half-filled level (tests/test_oracle_pins_closed_form.py); Anderson depth 0 is linear mixing and keeps
 a fixed point; at self-consistency the double-counting energy equals the direct
 functional T_s + int V_loc rho + E_NL + E_H + E_xc.
 The absolute SCF energies of the synthetic pseudo-atoms have no external value
@@ -214,7 +216,12 @@ def scf_init(grid: Grid, n_electrons: float, X0: np.ndarray, beta=0.3, depth=4) 
 
 def scf_step(ham: Hamiltonian, v_loc: np.ndarray, state: ScfState, n_electrons: float,
              kT: float, k_lobpcg: int = 3, first_maxit: int = 200, tol: float = 1e-6,
-             precond: str = "tpa") -> ScfOut:
+             precond: str = "tpa", later_tol: float = 0.0) -> ScfOut:
+    """One SCF step.  The first step converges LOBPCG to ``tol``; later steps
+    run ``k_lobpcg`` iterations, or, with ``later_tol > 0``, also converge to
+    ``later_tol`` (at most ``first_maxit`` iterations), which makes each step a
+    function of rho_in alone (the eigenpairs no longer depend on the iteration
+    path)."""
     grid = ham.grid
     dV = grid.dV
     v_eff, vh, eps_xc, vxc = effective_potential(grid, v_loc, state.rho_in)
@@ -223,6 +230,8 @@ def scf_step(ham: Hamiltonian, v_loc: np.ndarray, state: ScfState, n_electrons: 
     nocc = int(min(m, np.ceil(n_electrons / 2.0))) if kT <= 0 else m
     if state.step == 0:
         res = lobpcg(ham, state.X, maxit=first_maxit, tol=tol, nconv=nocc, precond=precond)
+    elif later_tol > 0.0:
+        res = lobpcg(ham, state.X, maxit=first_maxit, tol=later_tol, nconv=nocc, precond=precond)
     else:
         res = lobpcg(ham, state.X, maxit=k_lobpcg, tol=0.0, nconv=nocc, precond=precond)
     f, mu, S = occupations(res.eig, n_electrons, kT)

@@ -25,6 +25,7 @@ import numpy as np
 _STREAM_EKB = 0
 _STREAM_X0 = 1
 _STREAM_NN = 2
+_STREAM_PROBE = 3
 
 
 def diamond_sites(a: float, reps: int) -> np.ndarray:
@@ -59,6 +60,14 @@ def draw_x0(seed: int, nband: int, npts: int) -> np.ndarray:
     """Initial orbital block: complex standard normal, shape [nband][npts]."""
     rng = np.random.default_rng([seed, _STREAM_X0])
     re_im = rng.standard_normal((nband, npts, 2))
+    return re_im.view(np.complex128)[..., 0]
+
+
+def draw_probes(seed: int, nprobe: int, npts: int) -> np.ndarray:
+    """Probe block for subspace sketches: complex standard normal,
+    shape [nprobe][npts] (test infrastructure; not an input of the method)."""
+    rng = np.random.default_rng([seed, _STREAM_PROBE])
+    re_im = rng.standard_normal((nprobe, npts, 2))
     return re_im.view(np.complex128)[..., 0]
 
 
