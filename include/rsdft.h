@@ -246,7 +246,17 @@ typedef struct {
     int learned_iters;     /* RSDFT_PRECOND_LEARNED: add the network correction in
                               the first learned_iters iterations only, TPA alone
                               after them; 0 = in every iteration (default 0)      */
+    int refine;            /* RSDFT_MIXED, iterations after the FP32 phase:
+                              RSDFT_REFINE_FP32_CORRECTIONS (default) keeps X and
+                              HX in FP64 (residuals, residual norms, T_b, the X-X
+                              blocks of G_S and G_H, the X part of the rotation)
+                              and forms W = TPA(R), H W, P, H P and the Gram blocks
+                              that involve them on the FP32 path (recomputing H P
+                              each iteration); RSDFT_REFINE_FP64 runs them all in
+                              FP64.  Both stop on the FP64 residual norms.       */
 } rsdft_lobpcg_opts;
+
+enum { RSDFT_REFINE_FP64 = 0, RSDFT_REFINE_FP32_CORRECTIONS = 1 };
 
 typedef struct {
     int iterations;        /* full iterations done (both phases)                   */
@@ -311,6 +321,11 @@ typedef struct {
                               1e-4, then FP64 to tol) and the later steps' k_lobpcg
                               iterations on the FP32 data path                    */
     int tensor_cores;      /* as rsdft_lobpcg_opts.tensor_cores                    */
+    double later_tol;      /* 0 (default): the steps after the first run k_lobpcg
+                              LOBPCG iterations; > 0: they also converge to
+                              later_tol (at most first_maxit iterations; the mixed
+                              form as in the first solve), so that each step is a
+                              function of rho_in alone                            */
 } rsdft_scf_opts;
 
 typedef struct {
@@ -362,10 +377,18 @@ typedef enum {
     RSDFT_K_FFT_Z = 3,       /* z pass: forward, per-G factor, inverse          */
     RSDFT_K_FFT_XY_INV = 4,  /* xy-plane inverse pass (+ V psi + projectors)    */
     RSDFT_K_PROJECT = 5,     /* projector gather <beta|psi>                     */
-    RSDFT_K_DENSE = 6,       /* Cholesky, TRSM, eigensolve of the subspace      */
+    RSDFT_K_DENSE = 6,       /* the whole Rayleigh-Ritz solve of Eq. 1 (a group:
+                                the ids below time its parts)                   */
     RSDFT_K_GRAM_TC = 7,     /* tensor-core split-BF16 Gram (tcgen05)           */
     RSDFT_K_ROTATE_TC = 8,   /* tensor-core split-BF16 Ritz rotation (tcgen05)  */
-    RSDFT_K_COUNT = 9
+    RSDFT_K_CHOL = 9,        /* Cholesky of G_S with dropping: (4/3) k^3 flop   */
+    RSDFT_K_TRSM = 10,       /* the triangular solves of Eq. 1 and C = L^-H Z:
+                                4 k^2 per right-hand side                       */
+    RSDFT_K_TRIDIAG = 11,    /* Householder tridiagonalisation: (16/3) k^3      */
+    RSDFT_K_TRIEIG = 12,     /* bisection + inverse iteration on the tridiagonal
+                                matrix: k (3 x 52 + 20) per wanted eigenpair    */
+    RSDFT_K_BACKTRANSFORM = 13, /* Q Z in compact WY blocks: 8 k^2 per vector   */
+    RSDFT_K_COUNT = 14
 } rsdft_kernel_id;
 
 rsdft_status rsdft_profile_enable(rsdft_ctx *ctx, int on);

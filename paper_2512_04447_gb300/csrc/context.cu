@@ -253,7 +253,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     };
     void *olds[] = {w.X, w.HX, w.W, w.HW, w.P, w.HP, w.T1, w.Xn, w.HXn, w.Pn, w.HPn, w.Xs, w.proj,
                     w.GS, w.GH, w.C, w.Cfull, w.gram_part, w.Lm, w.Km, w.Ym, w.Vh, w.Zc,
-                    w.tau, w.wv, w.d, w.e, w.lam, w.zt, w.dscr, w.fac, w.gsync, w.drop, w.keep, w.ikeep,
+                    w.tau, w.wv, w.Tw, w.d, w.e, w.lam, w.zt, w.dscr, w.fac, w.gsync, w.drop, w.keep, w.ikeep,
                     w.theta, w.res, w.vexp, w.tkin, w.nrm, w.act};
     for (void *p : olds) release(p);
     if (w.hbuf) cudaFreeHost(w.hbuf);
@@ -274,6 +274,7 @@ rsdft_status ensure_workspace(rsdft_ctx *ctx, int nband) {
     RS_TRY(dev_alloc(ctx, (void **)&w.tau, k * sizeof(double2)));
     // the cooperative tridiagonalisation keeps w in two buffers of up to 4 parts
     RS_TRY(dev_alloc(ctx, (void **)&w.wv, 8 * k * sizeof(double2)));
+    RS_TRY(dev_alloc(ctx, (void **)&w.Tw, (k / 32 + 1) * 32 * 32 * sizeof(double2)));
     for (double **b : {&w.d, &w.e, &w.lam})
         RS_TRY(dev_alloc(ctx, (void **)b, k * sizeof(double)));
     RS_TRY(dev_alloc(ctx, (void **)&w.zt, k * k * sizeof(double)));

@@ -70,6 +70,51 @@ __device__ double block_sum(double v, double *sh) {
     return sh[32];
 }
 
+// ---- grid barrier of the cooperative kernels ----------------------------------------
+// Values written by other blocks of a cooperative launch are read with
+// ld.global.cg (L2, not the incoherent L1).  Every barrier wait is bounded: on
+// timeout the block sets the error flag and returns, and the others see the
+// flag and return.
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ double2 ldcg2(const double2 *p) { return __ldcg(p); }
+
+std::mutex &coop_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+// Grid barrier on a monotonic arrival counter (zeroed before the launch): the
+// e-th barrier of the launch completes when count reaches nblocks * (e + 1).
+// The wait is bounded by `limit` SM cycles; a block that gives up sets the
+// error flag, and blocks that see the flag stop waiting.
+__device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, int *s_ok, unsigned int &epoch) {
+    __threadfence();
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vcount = &g->count;
+        volatile int *verr = &g->err;
+        const unsigned int target = nblocks * epoch;
+        atomicAdd(&g->count, 1u);
+        const long long t0 = clock64();
+        while (*vcount < target) {
+            if (*verr) { ok = 0; break; }
+            if (clock64() - t0 > limit) { atomicExch(&g->err, 1); ok = 0; break; }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 // ---- Cholesky with dropping -----------------------------------------------------
 __global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double tol, double *out) {
     __shared__ double sh[33];
@@ -85,22 +130,24 @@ __global__ void k_maxdiag(const double2 *__restrict__ a, int k, int ld, double t
     }
 }
 
-// Factor columns kb..kb+nb-1 (rows kb..k-1, nb <= 32) in the lower triangle.
-// Every CTA factors the nb x nb diagonal block in shared memory (column c is
-// dropped when its Schur pivot is <= the floor: l_cc = 1 and L[c+1:, c] = 0);
-// CTA 0 writes it to diag_out with the drop flags.  Then each warp
-// solves one row i below the block, l_i = a_i L11^-H, by forward substitution
-// with lane c holding column c: the rows spread over the CTAs (one FP64 chain
-// of nb steps per row) instead of one CTA walking the whole panel.
-__global__ void __launch_bounds__(256)
-k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop, double2 *diag_out) {
-    __shared__ double2 sD[NBK][NBK + 1];
-    __shared__ double s_l[NBK], s_il[NBK];   // pivots and their reciprocals
-    __shared__ int s_drop[NBK];
-    const double floor_ = floorp[0];
+// Cholesky of G_S, right-looking in panels of NBK columns.  Per panel kb:
+//  (1) every CTA loads the nb x nb diagonal block and factors it in shared
+//      memory (column c is dropped when its Schur pivot is <= the floor:
+//      l_cc = 1 and L[c+1:, c] = 0);
+//  (2) the rows below the block, l_i = a_i L11^-H, one warp per row (lane c
+//      holds column c; one FP64 chain of nb steps per row);
+//  (3) the trailing update a_ij -= sum_c l_ic conj(l_jc), i >= j, in CHOL_TS
+//      square tiles spread over the CTAs.
+// One cooperative launch runs all panels with a grid barrier after (2) and
+// after (3); where the cooperative launch is refused, (1)+(2) and (3) run as
+// one launch each per panel.
+constexpr int CHOL_TS = 16;
+
+__device__ void chol_factor_diag(const double2 *a, int ld, int kb, int nb, double floor_,
+                                 double2 (*sD)[NBK + 1], double *s_l, double *s_il, int *s_drop) {
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
-        sD[r][c] = c <= r ? a[(size_t)(kb + r) * ld + kb + c] : make_double2(0.0, 0.0);
+        sD[r][c] = c <= r ? ldcg2(a + (size_t)(kb + r) * ld + kb + c) : make_double2(0.0, 0.0);
     }
     __syncthreads();
     for (int c = 0; c < nb; ++c) {
@@ -139,19 +186,16 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
         }
         __syncthreads();
     }
-    // the factored block goes to scratch, not back into a: other CTAs of this
-    // launch may not have read the original block yet (k_chol_update, the next
-    // launch, copies it into place)
-    if (blockIdx.x == 0) {
-        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) diag_out[t] = sD[t / nb][t % nb];
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
-    }
-    // rows below the diagonal block: warp per row, lane c = column kb + c
+}
+
+// Rows i >= kb+nb of the panel: l_i = a_i L11^-H by forward substitution, warp
+// wid of nw takes rows kb+nb+wid, kb+nb+wid+nw, ...
+__device__ void chol_panel_rows(double2 *a, int k, int ld, int kb, int nb, const double2 (*sD)[NBK + 1],
+                                const double *s_il, const int *s_drop, int wid, int nw) {
     const int lane = threadIdx.x & 31;
-    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
-    for (int i = kb + nb + (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); i < k; i += warps) {
+    for (int i = kb + nb + wid; i < k; i += nw) {
         double2 *row = a + (size_t)i * ld + kb;
-        double2 v = lane < nb ? row[lane] : make_double2(0.0, 0.0);
+        double2 v = lane < nb ? ldcg2(row + lane) : make_double2(0.0, 0.0);
         for (int c = 0; c < nb; ++c) {
             double2 x = make_double2(0.0, 0.0);
             if (lane == c && !s_drop[c]) {
@@ -171,30 +215,17 @@ k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, in
     }
 }
 
-// Trailing update a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]), i >= j >= kb+nb,
-// in CHOL_TS x CHOL_TS tiles (16: one entry per thread, and four times the tiles of a
-// 32-tile grid, so the FP64 work spreads over about twice as many SMs);
-// block (0, 0) also stores the panel's factored diagonal block from diag
-// (lower triangle) into a.  Launched with at least one block.
-constexpr int CHOL_TS = 16;
-__global__ void __launch_bounds__(256)
-k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restrict__ diag) {
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-            const int r = t / nb, c = t % nb;
-            if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = diag[t];
-        }
-    }
+// Trailing-update tile (ti, tj), ti >= tj, of the rows/columns >= kb+nb:
+// a[i][j] -= sum_{c in panel} l[i][c] conj(l[j][c]) for j <= i.
+__device__ void chol_update_tile(double2 *a, int k, int ld, int kb, int nb, int ti, int tj,
+                                 double2 (*Li)[NBK + 1], double2 (*Lj)[NBK + 1]) {
     const int t0 = kb + nb;
-    if (t0 >= k) return;
-    const int ti = blockIdx.y, tj = blockIdx.x;
-    if (tj > ti) return;
     const int i0 = t0 + ti * CHOL_TS, j0 = t0 + tj * CHOL_TS;
-    __shared__ double2 Li[CHOL_TS][NBK + 1], Lj[CHOL_TS][NBK + 1];
+    __syncthreads();   // the previous tile's readers of Li, Lj are done
     for (int t = threadIdx.x; t < CHOL_TS * nb; t += blockDim.x) {
         const int r = t / nb, c = t % nb;
-        Li[r][c] = (i0 + r < k) ? a[(size_t)(i0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
-        Lj[r][c] = (j0 + r < k) ? a[(size_t)(j0 + r) * ld + kb + c] : make_double2(0.0, 0.0);
+        Li[r][c] = (i0 + r < k) ? ldcg2(a + (size_t)(i0 + r) * ld + kb + c) : make_double2(0.0, 0.0);
+        Lj[r][c] = (j0 + r < k) ? ldcg2(a + (size_t)(j0 + r) * ld + kb + c) : make_double2(0.0, 0.0);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < CHOL_TS * CHOL_TS; t += blockDim.x) {
@@ -207,10 +238,95 @@ k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restri
             sx = fma(p.x, q.x, fma(p.y, q.y, sx));
             sy = fma(p.y, q.x, fma(-p.x, q.y, sy));
         }
-        double2 &x = a[(size_t)i * ld + j];
-        x.x -= sx;
-        x.y -= sy;
+        double2 *x = a + (size_t)i * ld + j;
+        const double2 x0 = ldcg2(x);
+        *x = make_double2(x0.x - sx, x0.y - sy);
     }
+}
+
+__device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    ti = r;
+    tj = t - r * (r + 1) / 2;
+}
+
+// All panels in one cooperative launch; drop flags to drop[0..k), and the
+// kept-column list (keep[0..kc), keep[k] = kc) at the end.
+__global__ void __launch_bounds__(256)
+k_chol_coop(double2 *a, int k, int ld, const double *floorp, int *drop, int *keep, GridSync *gs, long long limit) {
+    __shared__ double2 sD[NBK][NBK + 1];
+    __shared__ double2 Li[CHOL_TS][NBK + 1], Lj[CHOL_TS][NBK + 1];
+    __shared__ double s_l[NBK], s_il[NBK];
+    __shared__ int s_drop[NBK];
+    __shared__ int s_ok;
+    unsigned int epoch = 0;
+    const double floor_ = floorp[0];
+    const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+    const int wid = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    for (int kb = 0; kb < k; kb += NBK) {
+        const int nb = min(NBK, k - kb);
+        chol_factor_diag(a, ld, kb, nb, floor_, sD, s_l, s_il, s_drop);
+        if (blockIdx.x == 0)
+            for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
+        chol_panel_rows(a, k, ld, kb, nb, sD, s_il, s_drop, wid, nw);
+        const int rest = k - kb - nb;
+        if (rest > 0 && !grid_sync(gs, gridDim.x, limit, &s_ok, epoch)) return;
+        // every CTA has read the diagonal block: store its factor
+        if (blockIdx.x == 0) {
+            for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+                const int r = t / nb, c = t % nb;
+                if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = sD[r][c];
+            }
+        }
+        if (rest > 0) {
+            const int nt = (rest + CHOL_TS - 1) / CHOL_TS;
+            for (int t = blockIdx.x; t < nt * (nt + 1) / 2; t += gridDim.x) {
+                int ti, tj;
+                tri_index(t, ti, tj);
+                chol_update_tile(a, k, ld, kb, nb, ti, tj, Li, Lj);
+            }
+            if (!grid_sync(gs, gridDim.x, limit, &s_ok, epoch)) return;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int c = 0;
+        for (int i = 0; i < k; ++i)
+            if (!drop[i]) keep[c++] = i;
+        keep[k] = c;
+    }
+}
+
+// Fallback, one panel per pair of launches: (1)+(2) with the factored block
+// to diag_out (other CTAs of the launch may not have read the original yet),
+// then (3) with block (0, 0) storing the factored block from diag_out.
+__global__ void __launch_bounds__(256)
+k_chol_panel(double2 *a, int k, int ld, int kb, int nb, const double *floorp, int *drop, double2 *diag_out) {
+    __shared__ double2 sD[NBK][NBK + 1];
+    __shared__ double s_l[NBK], s_il[NBK];
+    __shared__ int s_drop[NBK];
+    chol_factor_diag(a, ld, kb, nb, floorp[0], sD, s_l, s_il, s_drop);
+    if (blockIdx.x == 0) {
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) diag_out[t] = sD[t / nb][t % nb];
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
+    }
+    chol_panel_rows(a, k, ld, kb, nb, sD, s_il, s_drop,
+                    (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)), (int)(gridDim.x * (blockDim.x >> 5)));
+}
+
+__global__ void __launch_bounds__(256)
+k_chol_update(double2 *a, int k, int ld, int kb, int nb, const double2 *__restrict__ diag) {
+    __shared__ double2 Li[CHOL_TS][NBK + 1], Lj[CHOL_TS][NBK + 1];
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int r = t / nb, c = t % nb;
+            if (c <= r) a[(size_t)(kb + r) * ld + kb + c] = diag[t];
+        }
+    }
+    if (kb + nb >= k || blockIdx.x > blockIdx.y) return;   // uniform over the block
+    chol_update_tile(a, k, ld, kb, nb, blockIdx.y, blockIdx.x, Li, Lj);
 }
 
 __global__ void k_keep_scan(const int *drop, int k, int *keep) {
@@ -250,149 +366,97 @@ __global__ void k_hermitise(const double2 *__restrict__ a, int lda, int kc, doub
 }
 
 // ---- triangular solves with the lower factor L (kc x kc) ----------------------------
-// Forward: solve L X = B in place (B: kc x ncol, ld ldb), one block row at a
-// time.  Diagonal block: one warp per right-hand-side column, lane r holds row
-// r; column-oriented substitution (x_c final, then rows below subtract it).
-__global__ void k_trsm_lower_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
-                                  double2 *b, int ldb, int ncol) {
-    __shared__ double2 Ls[NBK][NBK + 1];
-    __shared__ double Linv[NBK];   // reciprocal pivots, formed once per CTA
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
-    }
-    if (threadIdx.x < nb) Linv[threadIdx.x] = 1.0 / L[(size_t)(rb + threadIdx.x) * ldl + rb + threadIdx.x].x;
-    __syncthreads();
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (col >= ncol) return;   // whole warps
-    double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
-    for (int c = 0; c < nb; ++c) {
-        const double inv = Linv[c];   // real positive diagonal
-        double2 x = make_double2(v.x * inv, v.y * inv);
-        x.x = __shfl_sync(0xffffffffu, x.x, c);
-        x.y = __shfl_sync(0xffffffffu, x.y, c);
-        if (lane == c) v = x;
-        else if (lane > c && lane < nb) {
-            c_fms(v, Ls[lane][c], x);
+// All columns of B (kc x ncol, ld ldb) in place: BACK = false solves L X = B
+// (block rows of 32 from the top), BACK = true solves L^H X = B (from the
+// bottom).  Columns are independent, so there is no grid-wide step: one warp
+// per column, four columns per CTA; lane r holds row r of the current block
+// row.  For each block row the CTA stages the 32 x 32 tiles of L (of L^H) that
+// multiply the already solved block rows in shared memory, shared by its four
+// columns; the diagonal block is then solved by column-oriented substitution
+// (x_c final, the rows below subtract it).
+template <bool BACK>
+__global__ void __launch_bounds__(128)
+k_trsm_cols(const double2 *__restrict__ L, int ldl, int kc, double2 *b, int ldb, int ncol) {
+    __shared__ double2 Ts[32][33];
+    __shared__ double Linv[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.x * 4 + warp;
+    const bool act = col < ncol;          // uniform over the warp
+    const int nblk = (kc + 31) / 32;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int s = 0; s < nblk; ++s) {
+        const int rb = BACK ? nblk - 1 - s : s;
+        const int r0 = rb * 32, nr = min(32, kc - r0);
+        double2 acc = (act && lane < nr) ? b[(size_t)(r0 + lane) * ldb + col] : zero;
+        const int j_lo = BACK ? rb + 1 : 0, j_hi = BACK ? nblk : rb;
+        for (int jb = j_lo; jb < j_hi; ++jb) {
+            const int c0 = jb * 32, nc = min(32, kc - c0);
+            __syncthreads();   // the previous tile's readers are done
+            for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+                if (!BACK) {   // L[r0+r][c0+j], j fastest (coalesced)
+                    const int r = t >> 5, j = t & 31;
+                    Ts[r][j] = (r < nr && j < nc) ? L[(size_t)(r0 + r) * ldl + c0 + j] : zero;
+                } else {       // (L^H)[r0+r][c0+j] = conj(L[c0+j][r0+r]), r fastest (coalesced)
+                    const int j = t >> 5, r = t & 31;
+                    Ts[r][j] = (r < nr && j < nc) ? c_conj(L[(size_t)(c0 + j) * ldl + r0 + r]) : zero;
+                }
+            }
+            __syncthreads();
+            // solved rows c0.. of this column (written by this lane earlier)
+            const double2 xj = (act && lane < nc) ? b[(size_t)(c0 + lane) * ldb + col] : zero;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                double2 x;
+                x.x = __shfl_sync(0xffffffffu, xj.x, j);
+                x.y = __shfl_sync(0xffffffffu, xj.y, j);
+                c_fms(acc, Ts[lane][j], x);
+            }
         }
-    }
-    if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
-}
-
-// b[i][col] -= sum_{c<nb} L[i][rb+c] b[rb+c][col] for i in [rb+nb, kc); tiles of
-// TRSM_TR rows x 32 columns, one output per thread (small tiles balance the
-// FP64 work over the SMs).
-constexpr int TRSM_TR = 8;
-__global__ void __launch_bounds__(256)
-k_trsm_lower_update(const double2 *__restrict__ L, int ldl, int kc, int rb, int nb, double2 *b, int ldb,
-                    int ncol) {
-    const int i0 = rb + nb + blockIdx.y * TRSM_TR, c0 = blockIdx.x * 32;
-    __shared__ double2 Ls[TRSM_TR][NBK + 1], Xs[NBK][33];
-    for (int t = threadIdx.x; t < TRSM_TR * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        Ls[r][c] = (i0 + r < kc) ? L[(size_t)(i0 + r) * ldl + rb + c] : make_double2(0.0, 0.0);
-    }
-    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
-        const int xr = t / 32, xc = t % 32;
-        Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
-    const int i = i0 + r, col = c0 + s_;
-    if (i >= kc || col >= ncol) return;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = 0; c < nb; ++c) c_fma(acc, Ls[r][c], Xs[c][s_]);
-    double2 &x = b[(size_t)i * ldb + col];
-    x.x -= acc.x;
-    x.y -= acc.y;
-}
-
-// Backward: solve L^H X = B in place, block rows from the bottom.  Diagonal
-// block: one warp per column, lane r holds row r; (L^H)[r][c] = conj(L[c][r]).
-__global__ void k_trsm_upperH_diag(const double2 *__restrict__ L, int ldl, int rb, int nb,
-                                   double2 *b, int ldb, int ncol) {
-    __shared__ double2 Ls[NBK][NBK + 1];
-    __shared__ double Linv[NBK];   // reciprocal pivots, formed once per CTA
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        Ls[r][c] = L[(size_t)(rb + r) * ldl + rb + c];
-    }
-    if (threadIdx.x < nb) Linv[threadIdx.x] = 1.0 / L[(size_t)(rb + threadIdx.x) * ldl + rb + threadIdx.x].x;
-    __syncthreads();
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (col >= ncol) return;
-    double2 v = lane < nb ? b[(size_t)(rb + lane) * ldb + col] : make_double2(0.0, 0.0);
-    for (int c = nb - 1; c >= 0; --c) {
-        const double inv = Linv[c];
-        double2 x = make_double2(v.x * inv, v.y * inv);
-        x.x = __shfl_sync(0xffffffffu, x.x, c);
-        x.y = __shfl_sync(0xffffffffu, x.y, c);
-        if (lane == c) v = x;
-        else if (lane < c) {
-            c_fms(v, c_conj(Ls[c][lane]), x);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+            const int r = t >> 5, j = t & 31;
+            Ts[r][j] = (r < nr && j < nr) ? L[(size_t)(r0 + r) * ldl + r0 + j] : zero;
         }
+        if (threadIdx.x < nr) Linv[threadIdx.x] = 1.0 / L[(size_t)(r0 + threadIdx.x) * ldl + r0 + threadIdx.x].x;
+        __syncthreads();
+        double2 v = acc;
+        if (!BACK) {
+            for (int c = 0; c < nr; ++c) {
+                const double inv = Linv[c];   // real positive diagonal
+                double2 x = make_double2(v.x * inv, v.y * inv);
+                x.x = __shfl_sync(0xffffffffu, x.x, c);
+                x.y = __shfl_sync(0xffffffffu, x.y, c);
+                if (lane == c) v = x;
+                else if (lane > c && lane < nr) c_fms(v, Ts[lane][c], x);
+            }
+        } else {   // (L^H)[r][c] = conj(L[c][r])
+            for (int c = nr - 1; c >= 0; --c) {
+                const double inv = Linv[c];
+                double2 x = make_double2(v.x * inv, v.y * inv);
+                x.x = __shfl_sync(0xffffffffu, x.x, c);
+                x.y = __shfl_sync(0xffffffffu, x.y, c);
+                if (lane == c) v = x;
+                else if (lane < c) c_fms(v, c_conj(Ts[c][lane]), x);
+            }
+        }
+        if (act && lane < nr) b[(size_t)(r0 + lane) * ldb + col] = v;
     }
-    if (lane < nb) b[(size_t)(rb + lane) * ldb + col] = v;
-}
-
-// b[i][col] -= sum_{c<nb} conj(L[rb+c][i]) b[rb+c][col] for i in [0, rb); tiles as above.
-__global__ void __launch_bounds__(256)
-k_trsm_upperH_update(const double2 *__restrict__ L, int ldl, int rb, int nb, double2 *b, int ldb,
-                     int ncol) {
-    const int i0 = blockIdx.y * TRSM_TR, c0 = blockIdx.x * 32;
-    __shared__ double2 Ls[TRSM_TR][NBK + 1], Xs[NBK][33];
-    for (int t = threadIdx.x; t < TRSM_TR * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        Ls[r][c] = (i0 + r < rb) ? c_conj(L[(size_t)(rb + c) * ldl + i0 + r]) : make_double2(0.0, 0.0);
-    }
-    for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
-        const int xr = t / 32, xc = t % 32;
-        Xs[xr][xc] = (c0 + xc < ncol) ? b[(size_t)(rb + xr) * ldb + c0 + xc] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    const int r = threadIdx.x >> 5, s_ = threadIdx.x & 31;
-    const int i = i0 + r, col = c0 + s_;
-    if (i >= rb || col >= ncol) return;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = 0; c < nb; ++c) c_fma(acc, Ls[r][c], Xs[c][s_]);
-    double2 &x = b[(size_t)i * ldb + col];
-    x.x -= acc.x;
-    x.y -= acc.y;
 }
 
 static rsdft_status trsm_lower(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
                                int ldb, int ncol, cudaStream_t st) {
-    for (int rb = 0; rb < kc; rb += NBK) {
-        const int nb = std::min(NBK, kc - rb);
-        k_trsm_lower_diag<<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
-        count_launch(ctx);
-        const int rest = kc - rb - nb;
-        if (rest > 0) {
-            dim3 g(cdiv(ncol, 32), cdiv(rest, TRSM_TR));
-            k_trsm_lower_update<<<g, 256, 0, st>>>(L, ldl, kc, rb, nb, b, ldb, ncol);
-            count_launch(ctx);
-        }
-    }
+    if (kc <= 0 || ncol <= 0) return RSDFT_OK;
+    k_trsm_cols<false><<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, kc, b, ldb, ncol);
+    count_launch(ctx);
     RS_LAUNCHED(ctx, "trsm_lower");
     return RSDFT_OK;
 }
 
 static rsdft_status trsm_upperH(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, double2 *b,
                                 int ldb, int ncol, cudaStream_t st) {
-    const int nblk = cdiv(kc, NBK);
-    for (int q = nblk - 1; q >= 0; --q) {
-        const int rb = q * NBK;
-        const int nb = std::min(NBK, kc - rb);
-        k_trsm_upperH_diag<<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
-        count_launch(ctx);
-        if (rb > 0) {
-            dim3 g(cdiv(ncol, 32), cdiv(rb, TRSM_TR));
-            k_trsm_upperH_update<<<g, 256, 0, st>>>(L, ldl, rb, nb, b, ldb, ncol);
-            count_launch(ctx);
-        }
-    }
+    if (kc <= 0 || ncol <= 0) return RSDFT_OK;
+    k_trsm_cols<true><<<cdiv(ncol, 4), 128, 0, st>>>(L, ldl, kc, b, ldb, ncol);
+    count_launch(ctx);
     RS_LAUNCHED(ctx, "trsm_upperH");
     return RSDFT_OK;
 }
@@ -510,48 +574,7 @@ __global__ void k_house_rank2(double2 *a, int k, int ld, int i, const double2 *_
 // columns >= i+2 fused with the next matvec w_{i+1} = tau_{i+1} A^(i+1) v_{i+1}
 //                                                               -> grid barrier.
 // w alternates between two buffers (w_{i+1} is written while slower blocks may
-// still read w_i).  Values written by other blocks are read with ld.global.cg
-// (L2, not the incoherent L1).  Every barrier wait is bounded: on timeout the
-// block sets the error flag and returns, and the others see the flag and return.
-struct GridSync {
-    unsigned int count;
-    unsigned int gen;
-    int err;
-    int pad;
-};
-
-__device__ __forceinline__ double2 ldcg2(const double2 *p) { return __ldcg(p); }
-
-std::mutex &coop_mutex() {
-    static std::mutex m;
-    return m;
-}
-
-// Grid barrier on a monotonic arrival counter (zeroed before the launch): the
-// e-th barrier of the launch completes when count reaches nblocks * (e + 1).
-// The wait is bounded by `limit` SM cycles; a block that gives up sets the
-// error flag, and blocks that see the flag stop waiting.
-__device__ bool grid_sync(GridSync *g, unsigned int nblocks, long long limit, int *s_ok, unsigned int &epoch) {
-    __threadfence();
-    __syncthreads();
-    ++epoch;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned int *vcount = &g->count;
-        volatile int *verr = &g->err;
-        const unsigned int target = nblocks * epoch;
-        atomicAdd(&g->count, 1u);
-        const long long t0 = clock64();
-        while (*vcount < target) {
-            if (*verr) { ok = 0; break; }
-            if (clock64() - t0 > limit) { atomicExch(&g->err, 1); ok = 0; break; }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
+// still read w_i).
 
 // Block-wide sum of one complex value.
 __device__ double2 block_sum_c(double2 v, double2 *sh2) {
@@ -869,7 +892,7 @@ __global__ void k_tri_prep(const double *d, const double *e, int k, double *scr)
 // sub-interval that holds the j-th eigenvalue (counts are monotone in x, so
 // the points with count > j form a suffix); a round divides the bracket by 129
 // (against 33 with one warp, so about 30% fewer sequential rounds).  Stops at
-// a bracket of 4 ulps.
+// a bracket of 4 ulps of ||T||.
 constexpr int BIS_T = 128;
 __global__ void __launch_bounds__(BIS_T) k_bisect(const double *d, int k, int nkeep, const double *scr, double *lam) {
     const int j = blockIdx.x;
@@ -880,9 +903,13 @@ __global__ void __launch_bounds__(BIS_T) k_bisect(const double *d, int k, int nk
     const double *e2 = scr + 8;
     const double step = 1.0 / (double)(BIS_T + 1);
     double lo = scr[1], hi = scr[2];
+    // the bracket is final at 4 ulps of ||T|| (absolute, as in LAPACK's bisection
+    // with abstol = ulp ||T||): eigenvalues near zero need no more rounds than
+    // the others
+    const double tol_abs = 4.0 * DBL_EPSILON * fmax(scr[0], 1e-300);
     for (int round = 0; round < 40; ++round) {
         // lo and hi are the same in every thread (taken from shared memory)
-        if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+        if (hi - lo <= tol_abs) break;
         const double x = lo + (hi - lo) * ((double)(t + 1) * step);
         const int c = sturm_count(d, e2, k, x);
         const unsigned ball = __ballot_sync(0xffffffffu, c > j);
@@ -1043,105 +1070,104 @@ __global__ void k_cluster_gs(int k, int nkeep, const double *lam, const double *
     }
 }
 
-// z[:, j] = Q zt[j], Q = H(0) H(1) ... H(k-2); one CTA per column.
-__global__ void k_backtransform(int k, const double2 *__restrict__ vh, int ldv,
-                                const double2 *__restrict__ tau, const double *__restrict__ zt,
-                                double2 *z, int ldz) {
-    extern __shared__ double2 sz[];
-    __shared__ double2 sh2[33];
-    const int j = blockIdx.x;
+// ---- back-transformation, compact WY blocks of 32 reflectors -------------------------
+// Q = H(0) H(1) ... H(k-2), H(i) = I - tau_i v_i v_i^H, v_i stored in row i of
+// vh from column i+1 on (v_i[i+1] = 1; columns <= i are not part of it).  A
+// block of reflectors i0 .. i0+nr-1 is H(i0) ... H(i0+nr-1) = I - V T V^H with
+// T upper triangular (the forward, column-wise compact WY form of Schreiber and
+// Van Loan): T[j][j] = tau_j, T[0:j][j] = -tau_j T[0:j][0:j] (V[:, 0:j]^H v_j).
+constexpr int WY_NB = 32;
+
+// One CTA per block: S[a][j] = <v_a|v_j> (a < j, rows r > i0+j), then T column by
+// column in one warp; tw[blk][32][32] row-major.
+__global__ void __launch_bounds__(256)
+k_wy_tfactor(int k, const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tau,
+             double2 *__restrict__ tw) {
+    __shared__ double2 S[WY_NB][WY_NB + 1], T[WY_NB][WY_NB + 1];
+    const int i0 = blockIdx.x * WY_NB, nr = min(WY_NB, (k - 1) - i0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < WY_NB * WY_NB; p += nw) {
+        const int a = p / WY_NB, j = p % WY_NB;
+        if (a >= j || j >= nr) continue;   // uniform over the warp
+        const double2 *va = vh + (size_t)(i0 + a) * ldv, *vj = vh + (size_t)(i0 + j) * ldv;
+        double sx = 0.0, sy = 0.0;
+        for (int r = i0 + j + 1 + lane; r < k; r += 32) {   // conj(v_a) v_j
+            const double2 x = va[r], y = vj[r];
+            sx = fma(x.x, y.x, fma(x.y, y.y, sx));
+            sy = fma(x.x, y.y, fma(-x.y, y.x, sy));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) S[a][j] = make_double2(sx, sy);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int j = 0; j < WY_NB; ++j) {
+            const double2 tj = j < nr ? tau[i0 + j] : make_double2(0.0, 0.0);
+            double2 t = make_double2(0.0, 0.0);
+            if (lane < j && j < nr) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int c = lane; c < j; ++c) c_fma(acc, T[lane][c], S[c][j]);
+                t = c_mul(make_double2(-tj.x, -tj.y), acc);
+            } else if (lane == j) {
+                t = tj;
+            }
+            T[lane][j] = t;
+            __syncwarp();
+        }
+        double2 *out = tw + (size_t)blockIdx.x * WY_NB * WY_NB;
+        for (int c = 0; c < WY_NB; ++c) out[lane * WY_NB + c] = T[lane][c];
+    }
+}
+
+// z_j = Q zt_j for each wanted eigenvector j (one CTA each, the vector in shared
+// memory): blocks from the last to the first, z -= V (T (V^H z)).
+__global__ void __launch_bounds__(256)
+k_backtransform_wy(int k, const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tw,
+                   const double *__restrict__ zt, double2 *z, int ldz) {
+    extern __shared__ double2 sz[];   // [k]
+    __shared__ double2 y[WY_NB], u[WY_NB];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = threadIdx.x; r < k; r += blockDim.x) sz[r] = make_double2(zt[(size_t)j * k + r], 0.0);
     __syncthreads();
-    for (int i = k - 2; i >= 0; --i) {
-        const double2 t = tau[i];
-        if (t.x == 0.0 && t.y == 0.0) continue;
-        const double2 *v = vh + (size_t)i * ldv;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
-            const double2 p = c_mul(c_conj(v[r]), sz[r]);
-            acc.x += p.x;
-            acc.y += p.y;
+    const int nblk = (k - 1 + WY_NB - 1) / WY_NB;
+    for (int blk = nblk - 1; blk >= 0; --blk) {
+        const int i0 = blk * WY_NB, nr = min(WY_NB, (k - 1) - i0);
+        // y_a = <v_a|z>, rows r > i0 + a
+        for (int a = warp; a < nr; a += nw) {
+            const double2 *va = vh + (size_t)(i0 + a) * ldv;
+            double sx = 0.0, sy = 0.0;
+            for (int r = i0 + a + 1 + lane; r < k; r += 32) {
+                const double2 x = va[r], q = sz[r];
+                sx = fma(x.x, q.x, fma(x.y, q.y, sx));
+                sy = fma(x.x, q.y, fma(-x.y, q.x, sy));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lane == 0) y[a] = make_double2(sx, sy);
         }
-        acc = block_sum_c(acc, sh2);
-        const double2 f = c_mul(t, acc);
-        for (int r = i + 1 + threadIdx.x; r < k; r += blockDim.x) {
-            const double2 p = c_mul(f, v[r]);
-            sz[r].x -= p.x;
-            sz[r].y -= p.y;
+        __syncthreads();
+        if (warp == 0 && lane < nr) {   // u = T y, T upper triangular
+            const double2 *Tr = tw + (size_t)blk * WY_NB * WY_NB + lane * WY_NB;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = lane; c < nr; ++c) c_fma(acc, Tr[c], y[c]);
+            u[lane] = acc;
+        }
+        __syncthreads();
+        // z[r] -= sum_a v_a[r] u_a over a with r > i0 + a
+        for (int r = i0 + 1 + threadIdx.x; r < k; r += blockDim.x) {
+            double2 acc = sz[r];
+            const int amax = min(nr, r - i0);
+            for (int a = 0; a < amax; ++a) c_fms(acc, vh[(size_t)(i0 + a) * ldv + r], u[a]);
+            sz[r] = acc;
         }
         __syncthreads();
     }
     for (int r = threadIdx.x; r < k; r += blockDim.x) z[(size_t)r * ldz + j] = sz[r];
-}
-
-// Same, with row r of the vector held in registers by thread r % blockDim.x
-// (R rows per thread, k <= R blockDim.x): no barrier between reflectors besides
-// the one complex reduction, and the next reflector's elements are loaded
-// while the current one is applied.
-constexpr int BT_R = 4;
-__global__ void __launch_bounds__(1024)
-k_backtransform_reg(int k, const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tau,
-                    const double *__restrict__ zt, double2 *z, int ldz) {
-    __shared__ double2 sh2[33];
-    const int j = blockIdx.x, t = threadIdx.x, bd = blockDim.x;
-    double2 zr[BT_R], vc[BT_R], vn[BT_R];
-#pragma unroll
-    for (int q = 0; q < BT_R; ++q) {
-        const int r = t + q * bd;
-        zr[q] = make_double2(r < k ? zt[(size_t)j * k + r] : 0.0, 0.0);
-    }
-    int i = k - 2;
-    double2 tc = make_double2(0.0, 0.0);
-    if (i >= 0) {
-        tc = tau[i];
-#pragma unroll
-        for (int q = 0; q < BT_R; ++q) {
-            const int r = t + q * bd;
-            vc[q] = (r > i && r < k) ? vh[(size_t)i * ldv + r] : make_double2(0.0, 0.0);
-        }
-    }
-    for (; i >= 0; --i) {
-        double2 tn = make_double2(0.0, 0.0);
-        if (i > 0) {
-            tn = tau[i - 1];
-#pragma unroll
-            for (int q = 0; q < BT_R; ++q) {
-                const int r = t + q * bd;
-                vn[q] = (r > i - 1 && r < k) ? vh[(size_t)(i - 1) * ldv + r] : make_double2(0.0, 0.0);
-            }
-        }
-        if (tc.x != 0.0 || tc.y != 0.0) {   // uniform over the block
-            // v_i is zero on rows <= i: register slices q whose rows all lie
-            // there are skipped (the test is the same in every thread)
-            double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int q = 0; q < BT_R; ++q) {   // conj(v) z
-                if ((q + 1) * bd <= i + 1) continue;
-                acc.x = fma(vc[q].x, zr[q].x, acc.x);
-                acc.x = fma(vc[q].y, zr[q].y, acc.x);
-                acc.y = fma(vc[q].x, zr[q].y, acc.y);
-                acc.y = fma(-vc[q].y, zr[q].x, acc.y);
-            }
-            acc = block_sum_c(acc, sh2);
-            const double2 f = c_mul(tc, acc);
-#pragma unroll
-            for (int q = 0; q < BT_R; ++q) {   // z -= f v
-                if ((q + 1) * bd <= i + 1) continue;
-                zr[q].x = fma(-f.x, vc[q].x, zr[q].x);
-                zr[q].x = fma(f.y, vc[q].y, zr[q].x);
-                zr[q].y = fma(-f.x, vc[q].y, zr[q].y);
-                zr[q].y = fma(-f.y, vc[q].x, zr[q].y);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < BT_R; ++q) vc[q] = vn[q];
-        tc = tn;
-    }
-#pragma unroll
-    for (int q = 0; q < BT_R; ++q) {
-        const int r = t + q * bd;
-        if (r < k) z[(size_t)r * ldz + j] = zr[q];
-    }
 }
 
 rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
@@ -1159,7 +1185,9 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     const int ld = k;
     bool coop_done = false;
     std::unique_lock<std::mutex> coop_lock;
+    const double kd = (double)k;
     {
+        ProfScope ps(ctx, RSDFT_K_TRIDIAG, 16.0 / 3.0 * kd * kd * kd, 0.0, st, 0);
         // one cooperative launch for all Householder steps (occupancy queried once,
         // thread-safe static initialisation)
         static const int occ = [] {
@@ -1201,31 +1229,32 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
                 ctx->coop_last_error = (int)e;
             }
         }
+        for (int i = 0; i < k - 1 && !coop_done; ++i) {
+            const int L = k - i - 1;
+            k_house_reflector<<<1, 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.d, w.e);
+            count_launch(ctx);
+            k_house_matvec<<<cdiv((long long)L * 32, 256), 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.wv);
+            count_launch(ctx);
+            k_house_w<<<1, 256, 0, st>>>(k, i, w.Vh, k, w.tau, w.wv);
+            count_launch(ctx);
+            dim3 g(cdiv(L, 128), L);
+            k_house_rank2<<<g, 128, 0, st>>>(a, k, ld, i, w.Vh, k, w.wv);
+            count_launch(ctx);
+        }
+        if (!coop_done) {
+            k_house_last<<<1, 1, 0, st>>>(a, k, ld, w.d);
+            count_launch(ctx);
+        }
+        RS_LAUNCHED(ctx, "householder");
     }
-    for (int i = 0; i < k - 1 && !coop_done; ++i) {
-        const int L = k - i - 1;
-        k_house_reflector<<<1, 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.d, w.e);
-        count_launch(ctx);
-        k_house_matvec<<<cdiv((long long)L * 32, 256), 256, 0, st>>>(a, k, ld, i, w.Vh, k, w.tau, w.wv);
-        count_launch(ctx);
-        k_house_w<<<1, 256, 0, st>>>(k, i, w.Vh, k, w.tau, w.wv);
-        count_launch(ctx);
-        dim3 g(cdiv(L, 128), L);
-        k_house_rank2<<<g, 128, 0, st>>>(a, k, ld, i, w.Vh, k, w.wv);
-        count_launch(ctx);
-    }
-    if (!coop_done) {
-        k_house_last<<<1, 1, 0, st>>>(a, k, ld, w.d);
-        count_launch(ctx);
-    }
-    RS_LAUNCHED(ctx, "householder");
-    k_tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.dscr);
-    count_launch(ctx);
-    // one warp per eigenvalue and one CTA per warp: the Sturm counts and the
-    // substitutions are FP64 chains, so the eigenvalues spread over the SMs
-    k_bisect<<<nkeep, BIS_T, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
-    count_launch(ctx);
     {
+        ProfScope ps(ctx, RSDFT_K_TRIEIG, kd * nkeep * (3.0 * 52.0 + 20.0), 0.0, st, 0);
+        k_tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.dscr);
+        count_launch(ctx);
+        // one CTA per eigenvalue: the Sturm counts and the substitutions are FP64
+        // chains, so the eigenvalues spread over the SMs
+        k_bisect<<<nkeep, BIS_T, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+        count_launch(ctx);
         const size_t ii_smem = (size_t)6 * k * sizeof(double);
         static std::mutex ii_mutex;
         static size_t ii_smem_max = 0;
@@ -1241,18 +1270,30 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         }
         k_inverse_iter<<<nkeep, 32, use_smem ? ii_smem : 0, st>>>(w.d, w.e, k, nkeep, lam_dev, w.dscr,
                                                                    w.fac, w.zt, use_smem ? 1 : 0);
+        count_launch(ctx);
+        k_cluster_gs<<<nkeep, 256, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
+        count_launch(ctx);
     }
-    count_launch(ctx);
-    k_cluster_gs<<<nkeep, 256, 0, st>>>(k, nkeep, lam_dev, w.dscr, w.zt);
-    count_launch(ctx);
     {
-        const int bt_threads = std::max(32, cdiv(cdiv(k, BT_R), 32) * 32);
-        if (bt_threads <= 1024)
-            k_backtransform_reg<<<nkeep, bt_threads, 0, st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
-        else
-            k_backtransform<<<nkeep, 128, k * sizeof(double2), st>>>(k, w.Vh, k, w.tau, w.zt, z, ldz);
+        ProfScope ps(ctx, RSDFT_K_BACKTRANSFORM, 8.0 * kd * kd * nkeep, 0.0, st, 0);
+        const size_t bt_smem = (size_t)k * sizeof(double2);
+        static std::mutex bt_mutex;
+        static size_t bt_smem_max = 48 * 1024;
+        if (bt_smem > bt_smem_max) {
+            std::lock_guard<std::mutex> g(bt_mutex);
+            if (bt_smem > bt_smem_max && bt_smem <= 200 * 1024 &&
+                cudaFuncSetAttribute(k_backtransform_wy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bt_smem) == cudaSuccess)
+                bt_smem_max = bt_smem;
+            cudaGetLastError();
+        }
+        if (bt_smem > bt_smem_max)
+            return fail(ctx, RSDFT_E_INVALID, "subspace %d too large for the back-transformation", k);
+        k_wy_tfactor<<<cdiv(k - 1, WY_NB), 256, 0, st>>>(k, w.Vh, k, w.tau, w.Tw);
+        count_launch(ctx);
+        k_backtransform_wy<<<nkeep, 256, bt_smem, st>>>(k, w.Vh, k, w.Tw, w.zt, z, ldz);
+        count_launch(ctx);
     }
-    count_launch(ctx);
     RS_LAUNCHED(ctx, "tridiagonal eigensolve");
     if (coop_done) {
         // a barrier wait of the cooperative kernel that gave up leaves err set
@@ -1263,6 +1304,69 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         if (*slot != 0)
             return fail(ctx, RSDFT_E_TIMEOUT, "tridiagonalisation: a grid barrier wait timed out");
     }
+    return RSDFT_OK;
+}
+
+// Cholesky of w.Lm (k x k) with dropping, the floor in w.dscr[4]: one
+// cooperative launch, or one pair of launches per panel where the cooperative
+// launch is refused.  Leaves the drop flags in w.drop and the kept columns in
+// w.keep (keep[k] = their count).  After a cooperative launch *coop is set and
+// `lock` holds the process-wide cooperative-launch mutex, which the caller
+// releases once the stream has synchronised.
+static rsdft_status cholesky(rsdft_ctx *ctx, int k, cudaStream_t st, std::unique_lock<std::mutex> &lock,
+                             bool *coop) {
+    Workspace &w = ctx->ws;
+    *coop = false;
+    static const int occ = [] {
+        int dev = 0, cp = 0, o = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&cp, cudaDevAttrCooperativeLaunch, dev);
+        if (cp == 0 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_chol_coop, 256, 0) != cudaSuccess)
+            o = 0;
+        cudaGetLastError();
+        return o;
+    }();
+    if (occ > 0) {
+        lock = std::unique_lock<std::mutex>(coop_mutex());
+        const int rest = k - std::min(NBK, k);
+        const int nt = cdiv(rest, CHOL_TS);
+        // enough CTAs for one warp per panel row and one tile per CTA, at most one per SM
+        const int want = std::max(cdiv(k, 8), nt * (nt + 1) / 2);
+        const int nb = std::max(1, std::min(ctx->num_sms, want));
+        GridSync *gs = reinterpret_cast<GridSync *>(w.gsync);
+        RS_CUDA(ctx, cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+        long long limit = 4000000000LL;   // ~2 s of SM clock per barrier wait
+        double2 *a = w.Lm;
+        int kk = k, ld = k;
+        const double *fl = w.dscr + 4;
+        int *dr = w.drop, *kp = w.keep;
+        void *args[] = {&a, &kk, &ld, &fl, &dr, &kp, &gs, &limit};
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_chol_coop, dim3(nb), dim3(256), args, 0, st);
+        if (e == cudaSuccess) {
+            count_launch(ctx);
+            *coop = true;
+            RS_LAUNCHED(ctx, "cholesky");
+            return RSDFT_OK;
+        }
+        cudaGetLastError();
+        ++ctx->coop_fallbacks;
+        ctx->coop_last_error = (int)e;
+        lock.unlock();
+    }
+    for (int kb = 0; kb < k; kb += NBK) {
+        const int nb = std::min(NBK, k - kb);
+        // w.Km is free until the compaction: scratch for the factored block
+        k_chol_panel<<<std::max(1, cdiv(k - kb - nb, 8)), 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4,
+                                                                         w.drop, w.Km);
+        count_launch(ctx);
+        const int rest = k - kb - nb;
+        dim3 g(std::max(1, cdiv(rest, CHOL_TS)), std::max(1, cdiv(rest, CHOL_TS)));
+        k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.Km);
+        count_launch(ctx);
+    }
+    k_keep_scan<<<1, 1, 0, st>>>(w.drop, k, w.keep);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "cholesky");
     return RSDFT_OK;
 }
 
@@ -1282,30 +1386,27 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     if (nkeep > k || nkeep <= 0) return fail(ctx, RSDFT_E_INVALID, "bad nkeep");
     const size_t kk = (size_t)k * k;
     const double kd = (double)k;
-    ProfScope ps(ctx, RSDFT_K_DENSE, 8.0 * kd * kd * kd * (1.0 / 3.0 + 1.0 + 4.0 / 3.0) +
-                 8.0 * kd * kd * nkeep * 1.5, 0.0, st, 0);
+    ProfScope ps(ctx, RSDFT_K_DENSE, kd * kd * kd * (4.0 / 3.0 + 8.0 + 16.0 / 3.0) +
+                 kd * nkeep * (12.0 * kd + 176.0), 0.0, st, 0);
     RS_CUDA(ctx, cudaMemcpyAsync(w.Lm, gs, kk * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     k_maxdiag<<<1, 256, 0, st>>>(gs, k, k, pivot_tol, w.dscr + 4);
     count_launch(ctx);
-    for (int kb = 0; kb < k; kb += NBK) {
-        const int nb = std::min(NBK, k - kb);
-        // w.Km is free until the compaction below: scratch for the factored block
-        k_chol_panel<<<std::max(1, cdiv(k - kb - nb, 8)), 256, 0, st>>>(w.Lm, k, k, kb, nb, w.dscr + 4,
-                                                                         w.drop, w.Km);
-        count_launch(ctx);
-        const int rest = k - kb - nb;
-        dim3 g(std::max(1, cdiv(rest, CHOL_TS)), std::max(1, cdiv(rest, CHOL_TS)));
-        k_chol_update<<<g, 256, 0, st>>>(w.Lm, k, k, kb, nb, w.Km);
-        count_launch(ctx);
+    std::unique_lock<std::mutex> coop_lock;
+    bool coop = false;
+    {
+        ProfScope pc(ctx, RSDFT_K_CHOL, 4.0 / 3.0 * kd * kd * kd, 0.0, st, 0);
+        RS_TRY(cholesky(ctx, k, st, coop_lock, &coop));
     }
-    k_keep_scan<<<1, 1, 0, st>>>(w.drop, k, w.keep);
-    count_launch(ctx);
-    RS_LAUNCHED(ctx, "cholesky");
     int kc = 0;
-    double *slot = w.hbuf + w.hbuf_elems - 8;   // the front of hbuf holds LOBPCG residuals
+    int *slot = reinterpret_cast<int *>(w.hbuf + w.hbuf_elems - 8);   // the front of hbuf holds LOBPCG residuals
     RS_CUDA(ctx, cudaMemcpyAsync(slot, w.keep + k, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (coop)
+        RS_CUDA(ctx, cudaMemcpyAsync(slot + 1, &reinterpret_cast<GridSync *>(w.gsync)->err, sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaStreamSynchronize(st));
-    memcpy(&kc, slot, sizeof(int));
+    if (coop_lock.owns_lock()) coop_lock.unlock();
+    if (coop && slot[1] != 0) return fail(ctx, RSDFT_E_TIMEOUT, "cholesky: a grid barrier wait timed out");
+    kc = slot[0];
     if (ndropped) *ndropped = k - kc;
     if (kc < nkeep)
         return fail(ctx, RSDFT_E_NOT_SPD, "overlap has %d independent columns, %d wanted", kc, nkeep);
@@ -1317,19 +1418,26 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     k_gather_sq<<<cdiv(kc2, T), T, 0, st>>>(gh, k, w.keep, kc, w.Ym, kc);
     count_launch(ctx);
     RS_LAUNCHED(ctx, "compaction");
-    // first TRSM: Y = L^-1 G_H
-    RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Ym, kc, kc, st));
-    // second TRSM: K = L^-1 Y^H
-    k_conj_transpose<<<cdiv(kc2, T), T, 0, st>>>(w.Ym, kc, kc, w.Vh, kc);
-    count_launch(ctx);
-    RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Vh, kc, kc, st));
+    const double kcd = (double)kc;
+    {
+        ProfScope pt(ctx, RSDFT_K_TRSM, 8.0 * kcd * kcd * kcd, 0.0, st, 0);
+        // first TRSM: Y = L^-1 G_H
+        RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Ym, kc, kc, st));
+        // second TRSM: K = L^-1 Y^H
+        k_conj_transpose<<<cdiv(kc2, T), T, 0, st>>>(w.Ym, kc, kc, w.Vh, kc);
+        count_launch(ctx);
+        RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Vh, kc, kc, st));
+    }
     k_hermitise<<<cdiv(kc2, T), T, 0, st>>>(w.Vh, kc, kc, w.Ym, kc);
     count_launch(ctx);
     RS_LAUNCHED(ctx, "reduction");
     // eigenpairs of K (destroys Ym; the reflectors overwrite Vh)
     RS_TRY(eigh_lowest(ctx, w.Ym, kc, nkeep, lam_dev, w.Zc, nkeep, st));
     // C = L^-H Z
-    RS_TRY(trsm_upperH(ctx, w.Km, kc, kc, w.Zc, nkeep, nkeep, st));
+    {
+        ProfScope pt(ctx, RSDFT_K_TRSM, 4.0 * kcd * kcd * nkeep, 0.0, st, 0);
+        RS_TRY(trsm_upperH(ctx, w.Km, kc, kc, w.Zc, nkeep, nkeep, st));
+    }
     RS_CUDA(ctx, cudaMemsetAsync(c_out, 0, (size_t)k * nkeep * sizeof(double2), st));
     k_place_rows<<<cdiv((long long)kc * nkeep, T), T, 0, st>>>(w.Zc, kc, nkeep, w.keep, c_out);
     count_launch(ctx);

@@ -72,6 +72,7 @@ struct Workspace {
     // dense core scratch
     double2 *Lm = nullptr, *Km = nullptr, *Ym = nullptr, *Vh = nullptr, *Zc = nullptr;
     double2 *tau = nullptr, *wv = nullptr;
+    double2 *Tw = nullptr;   // compact-WY T factors of the reflector blocks [k/32][32][32]
     double *d = nullptr, *e = nullptr, *lam = nullptr, *zt = nullptr, *dscr = nullptr;
     double *fac = nullptr;   // inverse-iteration factors and vector [k][6][k] (shared-memory overflow)
     int *drop = nullptr, *keep = nullptr, *ikeep = nullptr;

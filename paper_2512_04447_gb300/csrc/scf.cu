@@ -347,11 +347,13 @@ void rsdft_scf_default_opts(rsdft_scf_opts *o) {
     o->precond = RSDFT_PRECOND_TPA;
     o->precision = RSDFT_FP64;
     o->tensor_cores = 0;
+    o->later_tol = 0.0;
 }
 
 static rsdft_status check_scf_opts(rsdft_ctx *ctx, const rsdft_scf_opts *o, int nband) {
     if (!o || !(o->n_electrons > 0.0) || o->n_electrons > 2.0 * nband || !(o->kT >= 0.0) ||
         o->depth < 0 || o->depth > 7 || o->k_lobpcg < 0 || o->first_maxit < 0 || !(o->tol >= 0.0) ||
+        !(o->later_tol >= 0.0) ||
         (o->precision != RSDFT_FP64 && o->precision != RSDFT_MIXED))
         return fail(ctx, RSDFT_E_INVALID, "bad SCF options");
     return RSDFT_OK;
@@ -404,6 +406,7 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     lo.precision = opts->precision;
     lo.tensor_cores = opts->tensor_cores;
     if (s.step == 0) { lo.maxit = opts->first_maxit; lo.tol = opts->tol; }
+    else if (opts->later_tol > 0.0) { lo.maxit = opts->first_maxit; lo.tol = opts->later_tol; }
     else { lo.maxit = opts->k_lobpcg; lo.tol = 0.0; lo.switch_tol = 0.0; }
     rsdft_lobpcg_stats ls{};
     rsdft_status lst = lobpcg_run(ctx, (double2 *)x_dev, nband, lo, nullptr, nullptr, &ls, st);
