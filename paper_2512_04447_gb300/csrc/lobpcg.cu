@@ -277,6 +277,49 @@ __global__ void k_convert(const A *__restrict__ in, long long cnt, B *__restrict
     }
 }
 
+// theta_b = Re<x_b|hx_b> / <x_b|x_b> (FP64): slice partials, then one thread per band
+__global__ void __launch_bounds__(RTHREADS)
+k_rq_part(const double2 *__restrict__ hx, const double2 *__restrict__ x, long long n, int S,
+          double2 *__restrict__ part) {
+    __shared__ double sh[33];
+    const int s_ = blockIdx.x, b = blockIdx.y;
+    long long i0, i1;
+    slice_of(n, S, s_, i0, i1);
+    const double2 *h = hx + (size_t)b * n, *xx = x + (size_t)b * n;
+    double s = 0.0, q = 0.0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double2 a = h[i], c = xx[i];
+        s = fma(c.x, a.x, fma(c.y, a.y, s));
+        q = fma(c.x, c.x, fma(c.y, c.y, q));
+    }
+    s = block_sum2(s, sh);
+    q = block_sum2(q, sh);
+    if (threadIdx.x == 0) part[(size_t)b * S + s_] = make_double2(s, q);
+}
+
+__global__ void k_rq_fin(const double2 *__restrict__ part, int S, int m, double *theta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    double s = 0.0, q = 0.0;
+    for (int j = 0; j < S; ++j) {
+        s += part[(size_t)b * S + j].x;
+        q += part[(size_t)b * S + j].y;
+    }
+    theta[b] = s / q;
+}
+
+// out += in, FP32 values added to an FP64 block
+__global__ void k_add_f32(double2 *out, const float2 *__restrict__ in, long long cnt) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 a = in[i];
+        double2 o = out[i];
+        o.x += (double)a.x;
+        o.y += (double)a.y;
+        out[i] = o;
+    }
+}
+
 // Precision dispatch of the building blocks.
 template <typename V> struct Ops;
 template <> struct Ops<double2> {
@@ -377,6 +420,7 @@ struct RunState {
     int iterations = 0;
     int dropped = 0;
     bool converged = false;   // max residual over nconv <= stop_tol
+    bool haveP = false;       // P and HP hold the last iteration's directions
 };
 
 // One LOBPCG run in precision V on the workspace.  x_in / x_out: [m][n] V.
@@ -557,6 +601,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         std::swap(X, Xn);
         std::swap(HX, HXn);
         haveP = true;
+        rs.haveP = true;
         ++it;
     }
     if (stats) {
@@ -569,6 +614,198 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
     w.X = (double2 *)X; w.Xn = (double2 *)Xn; w.HX = (double2 *)HX; w.HXn = (double2 *)HXn;
     if ((void *)x_out != (void *)X)
         RS_CUDA(ctx, cudaMemcpyAsync(x_out, X, (size_t)m * n * sizeof(V), cudaMemcpyDeviceToDevice, st));
+    return result;
+}
+
+// FP64 refinement of the mixed form with FP32 corrections.  X and HX are FP64:
+// the residuals and their norms, T_b, the X-X blocks of G_S and G_H and the X
+// part of the Ritz rotation are formed in FP64.  The corrections W = TPA(R),
+// HW = H W and the directions P, HP stay on the FP32 data path, with the Gram
+// blocks that involve them (split-BF16 tensor cores when tensor_cores >= 1):
+//  - an error e in a block that couples X to W or P moves the Ritz values by
+//    O(e^2 / gap) and X by O(e |C_WP|), and the coefficients C_WP of the
+//    corrections fall with the residual; the X-X blocks, which move the Ritz
+//    values by O(e), are FP64;
+//  - R is formed in FP64 before it is rounded, so W keeps FP32 relative accuracy
+//    however small the residual is;
+//  - HP = H P is recomputed from the normalised P every iteration (carried by
+//    the rotation, its FP32 rounding would be relative to |p|, which falls with
+//    the residual), so no P column needs to leave the basis;
+//  - the FP64 residual norms certify the tolerance.
+// P and HP of the FP32 phase (carryP) seed the first iteration.
+static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_opts &o, double stop_tol,
+                                  int maxit, bool carryP, RunState &rs, double *hres, rsdft_lobpcg_stats *stats,
+                                  cudaStream_t st) {
+    using B32 = RowBlocksT<float2>;
+    Workspace &w = ctx->ws;
+    const long long n = ctx->n;
+    const double dV = ctx->dV;
+    const int nconv = (o.nconv <= 0 || o.nconv > m) ? m : o.nconv;
+    double2 *X = w.X, *HX = w.HX, *Xn = w.Xn, *HXn = w.HXn;
+    float2 *W = (float2 *)w.W, *HW = (float2 *)w.HW, *P = (float2 *)w.P, *HP = (float2 *)w.HP;
+    float2 *Pn = (float2 *)w.Pn, *HPn = (float2 *)w.HPn, *T1 = (float2 *)w.T1;
+    float2 *Xs = w.Xs;
+    float2 *proj = (float2 *)w.proj;
+    int *hact = reinterpret_cast<int *>(w.hbuf + m);
+    int *hactp = reinterpret_cast<int *>(w.hbuf + 3 * m);
+    int *actp = w.act + m;
+    const bool tc = o.tensor_cores >= 1;
+    const bool tc_rot = o.tensor_cores >= 2;
+    const double pivot_tol = std::max(o.pivot_tol, PIVOT_TOL_FP32);
+    const double lock_tol = o.lock_tol;
+    if ((const void *)x != (const void *)X)
+        RS_CUDA(ctx, cudaMemcpyAsync(X, x, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    RS_TRY(apply_h64(ctx, X, HX, m, st));
+    {   // Rayleigh quotients of the (FP32-orthonormal) start
+        const int S = row_slices(ctx, m);
+        k_rq_part<<<dim3(S, m), RTHREADS, 0, st>>>(HX, X, n, S, w.gram_part);
+        k_rq_fin<<<cdiv(m, 128), 128, 0, st>>>(w.gram_part, S, m, w.theta);
+        count_launch(ctx, 2);
+        RS_LAUNCHED(ctx, "k_rq");
+    }
+    const long long cntm = (long long)m * n;
+    const int cgrid = std::min(cdiv(cntm, 256), 4096);
+    PhaseEvents pe;
+    if (stats) RS_TRY(pe.init(ctx));
+    bool haveP = carryP;
+    int it = 0;
+    rsdft_status result = RSDFT_OK;
+    for (;;) {
+        RS_TRY(resid_norms<double2>(ctx, HX, X, m, st));
+        RS_CUDA(ctx, cudaMemcpyAsync(hres, w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(ctx, cudaStreamSynchronize(st));
+        pe.collect(stats);
+        double rmax = 0.0;
+        bool bad = false;
+        for (int b = 0; b < m; ++b) {
+            if (!std::isfinite(hres[b])) bad = true;
+            if (b < nconv) rmax = std::max(rmax, hres[b]);
+        }
+        if (bad) { result = fail(ctx, RSDFT_E_NUMERIC, "non-finite residual at refinement iteration %d", it); break; }
+        rs.converged = rmax <= stop_tol;
+        if (rs.converged || it >= maxit) break;
+        int na = 0;
+        for (int b = 0; b < m; ++b)
+            if (hres[b] > lock_tol) hact[na++] = b;
+        if (na == 0) break;
+        int np_ = 0;
+        if (haveP)
+            for (int j = 0; j < na; ++j) hactp[np_++] = hact[j];
+        RS_CUDA(ctx, cudaMemcpyAsync(w.act, hact, na * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (np_ > 0) RS_CUDA(ctx, cudaMemcpyAsync(actp, hactp, np_ * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[0], st));
+        const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
+        const dim3 scalegrid(std::max(1, std::min(cdiv(n, 256 * 8), 256)), na);
+        // FP32 copy of X for the blocks that couple it to the corrections
+        k_convert<double2, float2><<<cgrid, 256, 0, st>>>(X, cntm, Xs);
+        // R = HX - X Theta of the active bands in FP64 (into Xn, free until the
+        // rotation), rounded to FP32 into W
+        k_residual_rows<double2><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, Xn);
+        k_convert<double2, float2><<<std::min(cdiv((long long)na * n, 256), 4096), 256, 0, st>>>(
+            Xn, (long long)na * n, W);
+        count_launch(ctx, 3);
+        RS_LAUNCHED(ctx, "refine residual");
+        if (o.precond == RSDFT_PRECOND_TPA || o.precond == RSDFT_PRECOND_LEARNED) {
+            RS_TRY(project32(ctx, Xs, proj, m, st));
+            k_tkin<float2><<<cdiv(na, 128), 128, 0, st>>>(w.theta, w.vexp, proj, ctx->pt, w.act, na, w.tkin);
+            count_launch(ctx);
+            RS_LAUNCHED(ctx, "k_tkin");
+            if (o.precond == RSDFT_PRECOND_LEARNED &&
+                (o.learned_iters <= 0 || rs.iterations + it < o.learned_iters)) {
+                // the network correction reads the residual rows, kept in T1
+                RS_CUDA(ctx, cudaMemcpyAsync(T1, W, (size_t)na * n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+                RS_TRY(fft_xy_forward32(ctx, Src::Plain, W, nullptr, nullptr, nullptr, Pn, na, st));
+                RS_TRY(fft_z_mid32(ctx, Mid::Tpa, Pn, w.tkin, na, st));
+                RS_TRY(fft_xy_inverse32(ctx, Pn, nullptr, nullptr, W, na, st));
+                RS_TRY(learned_correction<float2>(ctx, T1, na, W, st));
+            } else {
+                RS_TRY(fft_xy_forward32(ctx, Src::Plain, W, nullptr, nullptr, nullptr, T1, na, st));
+                RS_TRY(fft_z_mid32(ctx, Mid::Tpa, T1, w.tkin, na, st));
+                RS_TRY(fft_xy_inverse32(ctx, T1, nullptr, nullptr, W, na, st));
+            }
+        }
+        // W <- W - X <X|W> (FP32)
+        {
+            B32 YX{{Xs, nullptr, nullptr}, {m, 0, 0}};
+            B32 YW{{W, nullptr, nullptr}, {na, 0, 0}};
+            bool done = false;
+            if (tc) RS_TRY(gram_tc(ctx, YX, YW, w.C, na, st));
+            else RS_TRY(gram32(ctx, YX, YW, w.C, na, false, dV, st));
+            if (tc_rot && rotate_tc_fits(m + na, na)) {
+                RS_TRY(rotate_tc_ortho(ctx, m, na, w.C, W, st));
+                done = true;
+            }
+            if (!done) RS_TRY(rotate32(ctx, YX, w.C, na, na, W, -1, W, nullptr, st));
+        }
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[1], st));
+        RS_TRY(apply_h32(ctx, W, HW, na, st));
+        RS_TRY(row_norms<float2>(ctx, W, na, w.nrm, st));
+        k_scale_rows<float2><<<scalegrid, 256, 0, st>>>(W, HW, n, w.nrm);
+        count_launch(ctx);
+        RS_LAUNCHED(ctx, "normalise W");
+        if (np_ > 0) {
+            const dim3 pgrid(rowgrid.x, np_);
+            k_gather_rows<float2><<<pgrid, 256, 0, st>>>(P, HP, actp, n, Pn, HPn);
+            RS_TRY(row_norms<float2>(ctx, Pn, np_, w.nrm, st));
+            k_scale_rows<float2><<<dim3(scalegrid.x, np_), 256, 0, st>>>(Pn, nullptr, n, w.nrm);
+            count_launch(ctx, 2);
+            RS_LAUNCHED(ctx, "normalise P");
+            RS_TRY(apply_h32(ctx, Pn, HPn, np_, st));
+        }
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[2], st));
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[3], st));
+        const int k = m + na + np_;
+        // the X rows of HY enter only the X-X block of G_H, which is replaced
+        // by the FP64 block below: Xs stands in for them
+        B32 Y{{Xs, W, Pn}, {m, na, np_}};
+        B32 HY{{Xs, HW, HPn}, {m, na, np_}};
+        RS_TRY(gram_pair<float2>(ctx, Y, HY, w.GS, w.GH, k, tc, st));
+        {
+            RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
+            RowBlocks HYX{{HX, nullptr, nullptr}, {m, 0, 0}};
+            RS_TRY(gram(ctx, YX, YX, w.GS, k, true, dV, st));
+            RS_TRY(gram(ctx, YX, HYX, w.GH, k, true, dV, st));
+        }
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
+        int nd = 0;
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
+        rs.dropped += nd;
+        if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[5], st));
+        // P = [W P] C[m:], HP alike (FP32); X = X C[:m] + P, HX alike (FP64)
+        {
+            const double2 *cwp = w.Cfull + (size_t)m * m;
+            B32 YWP{{W, Pn, nullptr}, {na, np_, 0}};
+            B32 HYWP{{HW, HPn, nullptr}, {na, np_, 0}};
+            RS_TRY(rotate32(ctx, YWP, cwp, m, m, nullptr, 1, P, nullptr, st));
+            RS_TRY(rotate32(ctx, HYWP, cwp, m, m, nullptr, 1, HP, nullptr, st));
+            RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
+            RowBlocks HYX{{HX, nullptr, nullptr}, {m, 0, 0}};
+            RS_TRY(rotate(ctx, YX, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
+            RS_TRY(rotate(ctx, HYX, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
+            k_add_f32<<<cgrid, 256, 0, st>>>(Xn, P, cntm);
+            k_add_f32<<<cgrid, 256, 0, st>>>(HXn, HP, cntm);
+            count_launch(ctx, 2);
+            RS_LAUNCHED(ctx, "k_add_f32");
+        }
+        if (stats) {
+            RS_CUDA(ctx, cudaEventRecord(pe.ev[6], st));
+            pe.pending = true;
+        }
+        RS_CUDA(ctx, cudaMemcpyAsync(w.theta, w.lam, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::swap(X, Xn);
+        std::swap(HX, HXn);
+        haveP = true;
+        ++it;
+    }
+    if (stats) {
+        RS_CUDA(ctx, cudaStreamSynchronize(st));
+        pe.collect(stats);
+        pe.destroy();
+    }
+    rs.iterations += it;
+    w.X = X; w.Xn = Xn; w.HX = HX; w.HXn = HXn;
+    if ((void *)x != (void *)X)
+        RS_CUDA(ctx, cudaMemcpyAsync(x, X, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     return result;
 }
 
@@ -600,7 +837,10 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
         if (o.tol > 0.0 || rs.iterations < o.maxit) {
             RunState r2;
             const int left = o.tol > 0.0 ? std::max(0, o.maxit - rs.iterations) : o.maxit - rs.iterations;
-            r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
+            if (o.refine == RSDFT_REFINE_FP32_CORRECTIONS)
+                r = lobpcg_refine(ctx, x, m, o, o.tol, left, rs.haveP, r2, hres, stats, st);
+            else
+                r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
             rs.iterations += r2.iterations;
             rs.dropped += r2.dropped;
             rs.converged = r2.converged;
@@ -641,6 +881,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->switch_tol = 1e-4;
     o->tensor_cores = 0;
     o->learned_iters = 0;
+    o->refine = RSDFT_REFINE_FP32_CORRECTIONS;
 }
 
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
@@ -657,6 +898,8 @@ rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lo
         return fail(ctx, RSDFT_E_INVALID, "bad LOBPCG options");
     if (o.precision != RSDFT_FP64 && o.precision != RSDFT_MIXED)
         return fail(ctx, RSDFT_E_INVALID, "unknown precision");
+    if (o.refine != RSDFT_REFINE_FP64 && o.refine != RSDFT_REFINE_FP32_CORRECTIONS)
+        return fail(ctx, RSDFT_E_INVALID, "unknown refinement mode");
     if (o.precond != RSDFT_PRECOND_TPA && o.precond != RSDFT_PRECOND_NONE && o.precond != RSDFT_PRECOND_LEARNED)
         return fail(ctx, RSDFT_E_INVALID, "unknown preconditioner");
     if (o.precond == RSDFT_PRECOND_LEARNED && !ctx->nn.ready)

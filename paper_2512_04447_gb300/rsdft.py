@@ -23,6 +23,7 @@ OK, E_INVALID, E_GRID_NOT_5SMOOTH, E_OOM, E_CUDA, E_NOT_SPD, E_NUMERIC, E_TIMEOU
     E_NOT_CONVERGED = range(9)
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_TPA, PRECOND_LEARNED = 0, 1, 2
+REFINE_FP64, REFINE_FP32_CORRECTIONS = 0, 1
 NN_HIDDEN = 8
 NN_WEIGHTS = 27 * (2 * NN_HIDDEN + 2 * NN_HIDDEN * NN_HIDDEN + NN_HIDDEN)
 STATUS_NAMES = ["OK", "E_INVALID", "E_GRID_NOT_5SMOOTH", "E_OOM", "E_CUDA", "E_NOT_SPD",
@@ -51,7 +52,8 @@ class Projectors(C.Structure):
 class LobpcgOpts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("tol", C.c_double), ("nconv", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double),
-                ("switch_tol", C.c_double), ("tensor_cores", C.c_int), ("learned_iters", C.c_int)]
+                ("switch_tol", C.c_double), ("tensor_cores", C.c_int), ("learned_iters", C.c_int),
+                ("refine", C.c_int)]
 
 
 class LobpcgStats(C.Structure):
@@ -68,7 +70,7 @@ class ScfOpts(C.Structure):
     _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("beta", C.c_double),
                 ("depth", C.c_int), ("k_lobpcg", C.c_int), ("first_maxit", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
-                ("tensor_cores", C.c_int)]
+                ("tensor_cores", C.c_int), ("later_tol", C.c_double)]
 
 
 class ScfOut(C.Structure):
@@ -129,7 +131,7 @@ _PROTOS = {
 
 K_GRAM, K_ROTATE, K_FFT_XY_FWD, K_FFT_Z, K_FFT_XY_INV, K_PROJECT, K_DENSE, K_GRAM_TC = range(8)
 KERNEL_NAMES = ["gram", "rotate", "fft_xy_fwd", "fft_z", "fft_xy_inv", "project", "dense", "gram_tc",
-                "rotate_tc"]
+                "rotate_tc", "chol", "trsm", "tridiag", "trieig", "backtransform"]
 
 
 def lib() -> C.CDLL:
