@@ -545,6 +545,101 @@ def micro_dense(R, torch, sizes, reps):
     return out
 
 
+def _events_ms(torch, fn, reps):
+    """Mean CUDA-event time of fn() on the current stream (after one untimed call)."""
+    fn()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _grid_near(npts):
+    """A 5-smooth grid (N, N, N') with about npts points."""
+    best = None
+    smooth = [n for n in range(2, 129) if all(p in (2, 3, 5) for p in _factors(n))]
+    for a in smooth:
+        for c in smooth:
+            v = a * a * c
+            if best is None or abs(v - npts) < abs(best[0] - npts):
+                best = (v, (a, a, c))
+    return best[1]
+
+
+def _factors(n):
+    out, p = [], 2
+    while n > 1:
+        while n % p == 0:
+            out.append(p)
+            n //= p
+        p += 1
+    return out
+
+
+def micro_gram(R, torch, ks, ratio, reps):
+    """Gram G = Y^H Y of k rows over n ~ ratio * k points (the paper's Fig. 2b
+    shape: reduction length 250 times the output size), k around powers of two
+    (its Fig. 2a penalty at 2^p +- 1): FP64 on CUDA cores and split-BF16 x3 on
+    the tensor cores."""
+    import numpy as np
+    out = []
+    peak64 = _fp64_peak_tf()
+    peakbf = float(_peaks().get("bf16_tflops", 1955.4))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for k in ks:
+        N = _grid_near(ratio * k)
+        ctx = R.Context((10.0, 10.0, 10.0), N, np.zeros(N[0] * N[1] * N[2]))
+        n = ctx.n
+        y64 = torch.randn(k, n, dtype=torch.complex128, device="cuda", generator=g)
+        y32 = y64.to(torch.complex64)
+        gm = torch.empty(k, k, dtype=torch.complex128, device="cuda")
+        t64 = _events_ms(torch, lambda: ctx.gram(y64, y64, gm), reps)
+        t32 = _events_ms(torch, lambda: ctx.gram_bf16x3(y32, y32, gm), reps)
+        fl = 8.0 * n * k * k          # complex MACs of the full k x k product
+        out.append({"k": k, "n": n, "ratio": n / k, "grid": list(N),
+                    "fp64_ms": t64, "fp64_tflops": fl / t64 / 1e9, "fp64_frac": fl / t64 / 1e9 / peak64,
+                    "bf16x3_ms": t32, "bf16x3_tflops_effective": fl / t32 / 1e9,
+                    "bf16x3_tensor_frac": 3.0 * fl / t32 / 1e9 / peakbf})
+        del ctx, y64, y32
+        torch.cuda.empty_cache()
+    return out
+
+
+def micro_fft(R, torch, grids, batch, reps):
+    """The FFT Laplacian (forward 3D FFT, |G|^2/2, inverse; zero potential, no
+    projectors) per wavefunction, one band at a time and in a batch (the
+    paper's Fig. 4), FP64 and FP32."""
+    import numpy as np
+    out = []
+    hbm = float(_peaks().get("hbm_gbs", 6668.2))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for N in grids:
+        ctx = R.Context((10.0, 10.0, 10.0), (N, N, N), np.zeros(N ** 3))
+        n = ctx.n
+        rec = {"N": N}
+        for name, dt, prec, esz in (("fp64", torch.complex128, R.FP64, 16), ("fp32", torch.complex64, R.MIXED, 8)):
+            nb = batch if batch * n * esz * 2 < 60e9 else max(1, int(60e9 // (n * esz * 2)))
+            x = torch.randn(nb, n, dtype=dt, device="cuda", generator=g)
+            hx = torch.empty_like(x)
+            t1 = _events_ms(torch, lambda: ctx.apply_h(x[:1], hx[:1], precision=prec), reps)
+            tb = _events_ms(torch, lambda: ctx.apply_h(x, hx, precision=prec), max(1, reps // 4))
+            per = tb / nb
+            rec[name] = {"batch": nb, "ms_per_band_single": t1, "ms_per_band_batched": per,
+                         "batch_speedup": t1 / per,
+                         "batched_gbs_vs_read_write_once": 2.0 * n * esz / (per / 1e3) / 1e9,
+                         "frac_hbm_of_fused_bound": 2.0 * n * esz / (per / 1e3) / 1e9 / hbm}
+            del x, hx
+            torch.cuda.empty_cache()
+        out.append(rec)
+        del ctx
+    return out
+
+
 def run_micro(args):
     """Microbenches beside the paper's Figs 2-4: shapes to compare with the
     paper's curves, not targets (the paper's plots carry no numbers)."""
@@ -552,11 +647,104 @@ def run_micro(args):
 
     from paper_2512_04447_gb300 import rsdft as R
     torch.cuda.set_device(0)
-    res = {"fig3_subspace_solve": micro_dense(R, torch, [48, 432, 511, 512, 513, 1380, 1440], args.micro_reps)}
+    res = {"fig3_subspace_solve": micro_dense(R, torch, args.micro_sizes, args.micro_reps)}
+    if not args.micro_dense_only:
+        res["fig2_gram_shapes"] = micro_gram(R, torch, [127, 128, 129, 255, 256, 257, 511, 512, 513], 250,
+                                             args.micro_reps)
+        res["fig4_fft_batch"] = micro_fft(R, torch, [24, 32, 48, 64, 96, 128], 512, args.micro_reps)
     line = {"metric": "microbenches beside the paper's Figs 2-4", "impl": "ours", "n_gpus": 1,
             "data": "synthetic", "dtype": "f64 (dense core)",
-            "config": {"workload": "random Hermitian pairs (subspace solve); see each entry"},
+            "config": {"workload": "fig3: random Hermitian pairs (subspace solve of Eq. 1); fig2: Gram of "
+                                   "k random rows over ~250 k points; fig4: FFT Laplacian, 1 band vs a 512-band "
+                                   "batch (fewer where 60 GB would be exceeded)"},
             "fp64_peak_tflops": _fp64_peak_tf(), "results": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    """LOBPCG to 1e-6 Ha on a large fixed-potential cell: diamond216_96 (216 C,
+    96^3, 480 bands) or bcc128_120 (128 bcc atoms, 120^3, 460 bands, Z = 6), each
+    converged over the bands a zero-temperature filling occupies (432, 384).  The mixed form (FP32 data path, split-BF16 tensor-core
+    Gram matrices and rotations, FP64 dense core, then FP64 refinement) runs to
+    the tolerance; the plain FP64 form runs a few iterations from the same start,
+    and its time to the tolerance is estimated as its time per iteration times
+    the iterations the mixed form needed in all.  Each eigenvalue's error is
+    bounded from its final FP64 residual r_b and the gap g_b to the nearest other
+    Ritz value: |theta_b - lambda| <= r_b^2 / g_b (Kato-Temple) where r_b < g_b,
+    else r_b."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2512_04447_gb300 import rsdft as R
+    torch.cuda.set_device(0)
+    wl = workloads.REGISTRY[args.large]()
+    # the occupied bands of a zero-temperature filling; the rest are a buffer (the
+    # last computed band converges at the rate set by its gap to the first band
+    # not computed)
+    nconv = int(min(wl.nband, np.ceil(wl.n_electrons / 2)))
+    t0 = time.perf_counter()
+    ctx = R.context_for(wl)
+    x0 = wl.x0()
+    t_setup = time.perf_counter() - t0
+    x = torch.from_numpy(x0).cuda()
+    del x0
+    xs = x.clone()
+    warm = ctx.lobpcg_opts(maxit=1, tol=0.0, precision=R.MIXED, tensor_cores=2)
+    ctx.lobpcg(x, warm)
+    x.copy_(xs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ctx.profile_enable(True)
+    t0 = time.perf_counter()
+    eig, res, st, _ = ctx.lobpcg(x, ctx.lobpcg_opts(maxit=args.large_maxit, tol=1e-6, nconv=nconv,
+                                                    precision=R.MIXED, tensor_cores=2))
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    kern = {name: ctx.profile_read(kid) for kid, name in enumerate(R.KERNEL_NAMES)}
+    ctx.profile_enable(False)
+    # the plain FP64 form: a few iterations from the same start
+    x.copy_(xs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, st64, _ = ctx.lobpcg(x, ctx.lobpcg_opts(maxit=args.large_fp64_iters, tol=0.0, precision=R.FP64))
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    clocks = sampler.stop()
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6668.2))
+    kernels = {}
+    for k_, d in kern.items():
+        r_ = kernel_roofline(k_, d, "mixed_tc", sm_max, hbm)
+        if r_ is not None:
+            r_["ms_total"] = d["ms"]
+            r_["launches"] = d["launches"]
+            kernels[k_] = r_
+    # gap of each Ritz value to its neighbours (ascending); the last band's upper
+    # neighbour is outside the computed set, so it keeps the first-order bound
+    lo_gap = np.concatenate([[np.inf], np.diff(eig)])
+    hi_gap = np.concatenate([np.diff(eig), [0.0]])
+    gaps = np.minimum(lo_gap, hi_gap)
+    bound = np.where(res < gaps, res ** 2 / np.maximum(gaps, 1e-300), res)
+    line = {"metric": "LOBPCG time-to-1e-6 Ha, FP64 vs mixed, same GB300", "impl": "ours", "n_gpus": 1,
+            "unit": "s", "higher_is_better": False, "data": "synthetic", "dtype": "bf16x3+f32+f64",
+            "config": {"workload": f"{wl.name}: {wl.natom} atoms, {wl.N[0]}^3 grid, {wl.nband} bands, fixed V_loc, "
+                                   f"converged over {nconv} bands", "l2": "inputs larger than L2"},
+            "value": t_mixed,
+            "mixed": {"time_to_1e-6_s": t_mixed, "iterations": st.iterations, "iterations_fp32": st.iterations_mixed,
+                      "converged": bool(st.converged), "max_residual": float(np.max(res[:nconv])),
+                      "ms": {"hpsi": st.ms_hpsi, "precond": st.ms_precond, "gram": st.ms_gram, "dense": st.ms_dense,
+                             "rotate": st.ms_rotate, "other": st.ms_other}},
+            "fp64": {"iterations_run": st64.iterations, "s": t_fp64,
+                     "s_per_iteration": t_fp64 / max(1, st64.iterations),
+                     "time_to_1e-6_s_estimate": t_fp64 / max(1, st64.iterations) * st.iterations,
+                     "estimate": "FP64 time per iteration (initial H X and Rayleigh-Ritz included) x the mixed "
+                                 "form's total iterations"},
+            "eig_error_bound_max_Ha": float(np.max(bound[:nconv])),
+            "eig_error_bound_note": "per eigenvalue min(r_b, r_b^2/gap_b) from the final FP64 residuals",
+            "kernels": kernels, "setup_s": t_setup, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -770,11 +958,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed", "mixed_tc"])
-    ap.add_argument("--config", default="scf", choices=["scf", "batched", "learned", "micro"],
+    ap.add_argument("--config", default="scf", choices=["scf", "batched", "learned", "micro", "large"],
                     help="scf: the SCF-step line (default); batched: the uneven-cells batch line; "
                          "learned: train the learned preconditioner and judge it against TPA; "
-                         "micro: the microbenches beside the paper's Figs 2-4")
+                         "micro: the microbenches beside the paper's Figs 2-4; "
+                         "large: LOBPCG to 1e-6 Ha on a large cell (--large)")
+    ap.add_argument("--large", default="diamond216_96", choices=["diamond216_96", "bcc128_120"],
+                    help="large: the cell")
+    ap.add_argument("--large-maxit", type=int, default=200, help="large: iteration cap of the mixed form")
+    ap.add_argument("--large-fp64-iters", type=int, default=3, help="large: FP64 iterations timed")
     ap.add_argument("--micro-reps", type=int, default=5, help="micro: timed repetitions")
+    ap.add_argument("--micro-sizes", type=int, nargs="+", default=[48, 432, 511, 512, 513, 1380, 1440],
+                    help="micro: subspace sizes of the Eq. 1 solve")
+    ap.add_argument("--micro-dense-only", action="store_true", help="micro: the subspace solve only")
     ap.add_argument("--chem", default="both", choices=["both", "diamond", "bcc"], help="learned: chemistries")
     ap.add_argument("--train-steps", type=int, default=1500, help="learned: Adam steps")
     ap.add_argument("--train-batch", type=int, default=16, help="learned: samples per batch")
@@ -798,6 +994,9 @@ def main():
         return
     if args.config == "micro":
         run_micro(args)
+        return
+    if args.config == "large":
+        run_large(args)
         return
     if args.warmup < 1:
         ap.error("--warmup must be >= 1 (the first SCF step converges LOBPCG)")

@@ -186,7 +186,8 @@ rsdft_status rsdft_gram_sh_bf16x3(rsdft_ctx *ctx, const void *y_dev, const void 
  * as real GEMMs over the interleaved grid index with Y and C split into bf16
  * hi + lo and the products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM.
  * out0_dev, out1_dev: [m][n] complex64, caller-owned, must not alias y_dev.
- * Shape limits: 1 <= m <= 240 and k > m, else RSDFT_E_INVALID.  Relative
+ * Shape limits: m >= 1 and k > m, else RSDFT_E_INVALID (more than 240 bands
+ * are rotated in balanced groups of at most 240, one launch each).  Relative
  * error about 1e-5 of the largest |C[i][b] Y[i](r)| term. */
 rsdft_status rsdft_rotate_bf16x3(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
                                  void *out0_dev, void *out1_dev, void *stream);
@@ -235,14 +236,13 @@ typedef struct {
                               data path of RSDFT_MIXED uses at least 1e-3 and soft-
                               locks bands at residual <= 1e-6)                    */
     double switch_tol;     /* RSDFT_MIXED: FP32 data path until the max residual
-                              is <= max(tol, switch_tol) (1e-4) or stagnates (3
+                              is <= max(tol, switch_tol) (3e-5) or stagnates (3
                               iterations gaining < 10%), then FP64 to tol; 0 runs
                               FP32 iterations to maxit                            */
     int tensor_cores;      /* RSDFT_MIXED: 0 runs the FP32 phase's Gram matrices
                               and Ritz rotations on FP32 CUDA cores; 1 forms the
                               Gram matrices with split-BF16 tcgen05 GEMMs; 2 does
-                              the Ritz rotations that way too (when m <= 240)
-                              (default 0)                                         */
+                              the Ritz rotations that way too (default 0)         */
     int learned_iters;     /* RSDFT_PRECOND_LEARNED: add the network correction in
                               the first learned_iters iterations only, TPA alone
                               after them; 0 = in every iteration (default 0)      */
@@ -252,8 +252,10 @@ typedef struct {
                               blocks of G_S and G_H, the X part of the rotation)
                               and forms W = TPA(R), H W, P, H P and the Gram blocks
                               that involve them on the FP32 path (recomputing H P
-                              each iteration); RSDFT_REFINE_FP64 runs them all in
-                              FP64.  Both stop on the FP64 residual norms.       */
+                              each iteration; three iterations each gaining less
+                              than 10% hand over to the FP64 iterations);
+                              RSDFT_REFINE_FP64 runs them all in FP64.  Both stop
+                              on the FP64 residual norms.                         */
 } rsdft_lobpcg_opts;
 
 enum { RSDFT_REFINE_FP64 = 0, RSDFT_REFINE_FP32_CORRECTIONS = 1 };
@@ -317,9 +319,10 @@ typedef struct {
     double tol;            /* residual tolerance of the first solve (1e-6)         */
     int precond;           /* rsdft_precond                                        */
     int precision;         /* rsdft_precision of the LOBPCG: RSDFT_MIXED runs the
-                              first solve in the mixed form (FP32 data path to
-                              1e-4, then FP64 to tol) and the later steps' k_lobpcg
-                              iterations on the FP32 data path                    */
+                              first solve in the mixed form (FP32 data path to the
+                              default switch_tol, then the default refinement to
+                              tol) and the later steps' k_lobpcg iterations on the
+                              FP32 data path                                      */
     int tensor_cores;      /* as rsdft_lobpcg_opts.tensor_cores                    */
     double later_tol;      /* 0 (default): the steps after the first run k_lobpcg
                               LOBPCG iterations; > 0: they also converge to

@@ -375,10 +375,23 @@ __global__ void k_hermitise(const double2 *__restrict__ a, int lda, int kc, doub
 // columns; the diagonal block is then solved by column-oriented substitution
 // (x_c final, the rows below subtract it).
 template <bool BACK>
+__device__ __forceinline__ double2 trsm_tile_elem(const double2 *__restrict__ L, int ldl, int r0, int nr, int c0,
+                                                  int nc, int t) {
+    if (!BACK) {   // L[r0+r][c0+j], j fastest (coalesced)
+        const int r = t >> 5, j = t & 31;
+        return (r < nr && j < nc) ? L[(size_t)(r0 + r) * ldl + c0 + j] : make_double2(0.0, 0.0);
+    }
+    // (L^H)[r0+r][c0+j] = conj(L[c0+j][r0+r]), r fastest (coalesced)
+    const int j = t >> 5, r = t & 31;
+    return (r < nr && j < nc) ? c_conj(L[(size_t)(c0 + j) * ldl + r0 + r]) : make_double2(0.0, 0.0);
+}
+
+template <bool BACK>
 __global__ void __launch_bounds__(128)
 k_trsm_cols(const double2 *__restrict__ L, int ldl, int kc, double2 *b, int ldb, int ncol) {
     __shared__ double2 Ts[32][33];
     __shared__ double Linv[32];
+    constexpr int PER = 32 * 32 / 128;   // tile elements staged per thread
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int col = blockIdx.x * 4 + warp;
     const bool act = col < ncol;          // uniform over the warp
@@ -389,19 +402,29 @@ k_trsm_cols(const double2 *__restrict__ L, int ldl, int kc, double2 *b, int ldb,
         const int r0 = rb * 32, nr = min(32, kc - r0);
         double2 acc = (act && lane < nr) ? b[(size_t)(r0 + lane) * ldb + col] : zero;
         const int j_lo = BACK ? rb + 1 : 0, j_hi = BACK ? nblk : rb;
+        // the next tile is fetched into registers while the current one is used
+        double2 pre[PER];
+        if (j_lo < j_hi) {
+            const int c0 = j_lo * 32, nc = min(32, kc - c0);
+#pragma unroll
+            for (int q = 0; q < PER; ++q) pre[q] = trsm_tile_elem<BACK>(L, ldl, r0, nr, c0, nc, threadIdx.x + q * 128);
+        }
         for (int jb = j_lo; jb < j_hi; ++jb) {
             const int c0 = jb * 32, nc = min(32, kc - c0);
             __syncthreads();   // the previous tile's readers are done
-            for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-                if (!BACK) {   // L[r0+r][c0+j], j fastest (coalesced)
-                    const int r = t >> 5, j = t & 31;
-                    Ts[r][j] = (r < nr && j < nc) ? L[(size_t)(r0 + r) * ldl + c0 + j] : zero;
-                } else {       // (L^H)[r0+r][c0+j] = conj(L[c0+j][r0+r]), r fastest (coalesced)
-                    const int j = t >> 5, r = t & 31;
-                    Ts[r][j] = (r < nr && j < nc) ? c_conj(L[(size_t)(c0 + j) * ldl + r0 + r]) : zero;
-                }
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int t = threadIdx.x + q * 128;
+                if (!BACK) Ts[t >> 5][t & 31] = pre[q];
+                else Ts[t & 31][t >> 5] = pre[q];
             }
             __syncthreads();
+            if (jb + 1 < j_hi) {
+                const int c1 = c0 + 32, nc1 = min(32, kc - c1);
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    pre[q] = trsm_tile_elem<BACK>(L, ldl, r0, nr, c1, nc1, threadIdx.x + q * 128);
+            }
             // solved rows c0.. of this column (written by this lane earlier)
             const double2 xj = (act && lane < nc) ? b[(size_t)(c0 + lane) * ldb + col] : zero;
 #pragma unroll 8
@@ -1026,13 +1049,17 @@ k_inverse_iter(const double *d, const double *e, int k, int nkeep, const double 
 
 // Gram-Schmidt (two passes) of each vector against the earlier vectors of its
 // eigenvalue cluster (a maximal run of consecutive eigenvalues with gaps of at
-// most 1e-3 ||T||), then normalisation.  Clusters are independent: CTA j
-// handles the cluster that starts at eigenvalue j; singletons are left as
-// inverse iteration normalised them.
+// most 1e-6 ||T||), then normalisation.  Inverse iteration leaves two vectors
+// whose eigenvalues are g apart orthogonal to about eps ||T|| / g, so outside
+// such clusters the loss is below 3e-10; a wider threshold (LAPACK's 1e-3 ||T||)
+// merged hundreds of distinct eigenvalues of a 1440 x 1440 problem into one
+// cluster, whose Gram-Schmidt on one CTA then took most of the solve.  Clusters
+// are independent: CTA j handles the cluster that starts at eigenvalue j;
+// singletons are left as inverse iteration normalised them.
 __global__ void k_cluster_gs(int k, int nkeep, const double *lam, const double *scr, double *zt) {
     __shared__ double sh[33];
     __shared__ double dots[1024];
-    const double ortol = 1e-3 * scr[0];
+    const double ortol = 1e-6 * scr[0];
     const int cstart = blockIdx.x;
     if (cstart >= nkeep) return;
     if (cstart > 0 && lam[cstart] - lam[cstart - 1] <= ortol) return;   // not a cluster start

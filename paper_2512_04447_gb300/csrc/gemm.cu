@@ -37,9 +37,11 @@ __device__ __forceinline__ void upper_tile(int t, int T, int &ti, int &tj) {
 // mixed form: FP32 products and accumulation inside the CTA); the partials are
 // stored in FP64 and reduced in FP64 by k_gram_reduce.  Output tile edge 16*P
 // (each of the 16 x 16 threads owns P x P entries).
-template <typename V, int P>
+// VB is the type of B's rows: V, or float2 with V = double2 (FP32 rows against
+// FP64 rows, converted exactly and multiplied in FP64).
+template <typename V, typename VB, int P>
 __global__ void __launch_bounds__(GTHREADS)
-k_gram_partial(RowBlocksT<V> A, RowBlocksT<V> B, int na, int nb, long long n, int hermitian, int Ti,
+k_gram_partial(RowBlocksT<V> A, RowBlocksT<VB> B, int na, int nb, long long n, int hermitian, int Ti,
                int Tj, long long kchunk, double2 *__restrict__ part) {
     using T = decltype(V{}.x);
     constexpr int TE = 16 * P;
@@ -69,7 +71,11 @@ k_gram_partial(RowBlocksT<V> A, RowBlocksT<V> B, int na, int nb, long long n, in
             va.x = va.y = vb.x = vb.y = (T)0;
             if (kk < k1) {
                 if (i0 + lrow < na) va = row_of(A, i0 + lrow, n)[kk];
-                if (j0 + lrow < nb) vb = row_of(B, j0 + lrow, n)[kk];
+                if (j0 + lrow < nb) {
+                    const VB t = row_of(B, j0 + lrow, n)[kk];
+                    vb.x = (T)t.x;
+                    vb.y = (T)t.y;
+                }
             }
             As[lk][lrow] = va;
             Bs[lk][lrow] = vb;
@@ -191,12 +197,12 @@ static int pick_splits(int tiles, long long n, int capacity) {
     return best;
 }
 
-template <typename V, int P>
-static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B,
+template <typename V, typename VB, int P>
+static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<VB> &B,
                                 int na, int nb, double2 *g, int ldg, bool hermitian, double scale,
                                 cudaStream_t st) {
     constexpr int TE = 16 * P;
-    static int occ = occupancy(k_gram_partial<V, P>, GTHREADS);
+    static int occ = occupancy(k_gram_partial<V, VB, P>, GTHREADS);
     const int Ti = cdiv(na, TE), Tj = cdiv(nb, TE);
     const int tiles = hermitian ? Ti * (Ti + 1) / 2 : Ti * Tj;
     const long long n = ctx->n;
@@ -207,12 +213,14 @@ static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const Ro
     RS_TRY(ensure_gram_part(ctx, (size_t)nsplit * na * nb));
     dim3 grid(tiles, nsplit);
     {
-        const bool same = A.ptr[0] == B.ptr[0] && A.ptr[1] == B.ptr[1] && A.ptr[2] == B.ptr[2];
+        const bool same = (const void *)A.ptr[0] == (const void *)B.ptr[0] &&
+                          (const void *)A.ptr[1] == (const void *)B.ptr[1] &&
+                          (const void *)A.ptr[2] == (const void *)B.ptr[2];
         const double entries = hermitian ? 0.5 * na * (na + 1.0) : (double)na * nb;
         ProfScope ps(ctx, RSDFT_K_GRAM, 8.0 * (double)n * entries,
-                     (double)sizeof(V) * (double)n * (same ? na : na + nb), st);
-        k_gram_partial<V, P><<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj,
-                                                        kchunk, ctx->ws.gram_part);
+                     (double)n * (same ? sizeof(V) * na : sizeof(V) * na + sizeof(VB) * nb), st);
+        k_gram_partial<V, VB, P><<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj,
+                                                            kchunk, ctx->ws.gram_part);
     }
     RS_LAUNCHED(ctx, "k_gram_partial");
     const long long tot = (long long)na * nb;
@@ -223,8 +231,8 @@ static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const Ro
     return RSDFT_OK;
 }
 
-template <typename V>
-rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B, double2 *g, int ldg,
+template <typename V, typename VB = V>
+rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<VB> &B, double2 *g, int ldg,
                     bool hermitian, double scale, cudaStream_t st) {
     const int na = A.cnt[0] + A.cnt[1] + A.cnt[2];
     const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
@@ -233,13 +241,14 @@ rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> 
     // tile edge 16 P, P in {2, 3, 4}: the least-padding rule, or the autotuner's pick
     auto run = [&](int c) -> rsdft_status {
         switch (c + 2) {
-            case 2: return gram_launch<V, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-            case 3: return gram_launch<V, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-            default: return gram_launch<V, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            case 2: return gram_launch<V, VB, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            case 3: return gram_launch<V, VB, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            default: return gram_launch<V, VB, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
         }
     };
     // shapes in buckets of 32 (the subspace size changes as bands lock)
-    const std::string key = std::string(sizeof(V) == 8 ? "gram32 " : "gram64 ") + std::to_string(cdiv(na, 32)) +
+    const std::string key = std::string(sizeof(V) == 8 ? "gram32 " : (sizeof(VB) == 8 ? "gram64x32 " : "gram64 ")) +
+                            std::to_string(cdiv(na, 32)) +
                             " " + std::to_string(cdiv(nb, 32)) + (hermitian ? " h" : " g");
     int chosen = 0;
     return autotune_pick(ctx, key, 3, pick_p(na, nb) - 2, st, run, &chosen);
@@ -252,6 +261,10 @@ rsdft_status gram(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, double
 rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
                     double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st) {
     return gram_t<float2>(ctx, A, B, g, ldg, hermitian, scale, st);
+}
+rsdft_status gram64x32(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocksT<float2> &B, double2 *g, int ldg,
+                       double scale, cudaStream_t st) {
+    return gram_t<double2, float2>(ctx, A, B, g, ldg, false, scale, st);
 }
 
 // ---- rotation ----------------------------------------------------------------------
@@ -475,7 +488,7 @@ rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int
     RowBlocks B{{(const double2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
     // every partial entry the reduction reads is written by this launch first,
     // so nothing left by an earlier call is read
-    k_gram_partial<double2, 4><<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
+    k_gram_partial<double2, double2, 4><<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_partial: %s", cudaGetErrorString(e));
     k_gram_reduce<<<cdiv((long long)na * nb, 256), 256, 0, st>>>(part, nsplit, na, nb, 0, GT, scale,

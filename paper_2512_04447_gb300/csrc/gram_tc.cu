@@ -997,6 +997,26 @@ static rsdft_status rotate_launch(rsdft_ctx *ctx, const RotSpec &sp, cudaStream_
     return check_err(ctx, st);
 }
 
+// More output bands than one TMEM accumulator pair holds (MAX_NH): the bands go
+// in chunks of at most MAX_NH (multiples of 16, balanced), one launch each;
+// every chunk reads all the split rows of Y again.
+static rsdft_status rotate_chunked(rsdft_ctx *ctx, const RotSpec &sp, cudaStream_t st) {
+    if (sp.ncol <= MAX_NH) return rotate_launch(ctx, sp, st);
+    const int nchunk = cdiv(sp.ncol, MAX_NH);
+    const int mc = cdiv(cdiv(sp.ncol, nchunk), 16) * 16;
+    const long long n = ctx->n;
+    for (int b0 = 0; b0 < sp.ncol; b0 += mc) {
+        RotSpec c = sp;
+        c.c = sp.c + b0;
+        c.ncol = std::min(mc, sp.ncol - b0);
+        c.out0 = sp.out0 ? sp.out0 + (size_t)b0 * n : nullptr;
+        c.out1 = sp.out1 ? sp.out1 + (size_t)b0 * n : nullptr;
+        c.base = sp.base ? sp.base + (size_t)b0 * n : nullptr;
+        RS_TRY(rotate_launch(ctx, c, st));
+    }
+    return RSDFT_OK;
+}
+
 // Ritz rotation of split rows row0 .. row0 + k of b's B region (X = the first m rows).
 static rsdft_status rotate_rows(rsdft_ctx *ctx, const Buffers &b, int row0, int k, const double2 *c, int ldc,
                                 int m, float2 *out0, float2 *out1, cudaStream_t st) {
@@ -1016,7 +1036,7 @@ static rsdft_status rotate_rows(rsdft_ctx *ctx, const Buffers &b, int row0, int 
     sp.out1 = out1;
     sp.base = nullptr;
     sp.sign = 1;
-    return rotate_launch(ctx, sp, st);
+    return rotate_chunked(ctx, sp, st);
 }
 
 }  // namespace tc
@@ -1070,7 +1090,7 @@ rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlock
 // W <- W - X C (C = <X|W>, m x na, ld na) on the tensor cores, from the X split
 // rows that the preceding gram_tc(X, W) left in the A region of the workspace.
 rsdft_status rotate_tc_ortho(rsdft_ctx *ctx, int m, int na, const double2 *c, float2 *w, cudaStream_t st) {
-    if (m < 1 || na < 1 || cdiv(na, 16) * 16 > tc::MAX_NH)
+    if (m < 1 || na < 1)
         return fail(ctx, RSDFT_E_INVALID, "tensor-core orthogonalisation: m %d, na %d", m, na);
     tc::Buffers b;
     RS_TRY(tc::buffers(ctx, m, na, b));   // the layout gram_tc(X, W) wrote
@@ -1089,15 +1109,15 @@ rsdft_status rotate_tc_ortho(rsdft_ctx *ctx, int m, int na, const double2 *c, fl
     sp.out1 = nullptr;
     sp.base = w;
     sp.sign = -1;
-    return tc::rotate_launch(ctx, sp, st);
+    return tc::rotate_chunked(ctx, sp, st);
 }
 
-bool rotate_tc_fits(int k, int m) { return m >= 1 && k > m && cdiv(m, 16) * 16 <= tc::MAX_NH; }
+bool rotate_tc_fits(int k, int m) { return m >= 1 && k > m; }
 
 rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
                              float2 *out0, float2 *out1, cudaStream_t st) {
     // k == m (X only, no new P) is allowed when out1 is NULL
-    const bool ok = rotate_tc_fits(k, m) || (k == m && !out1 && m >= 1 && cdiv(m, 16) * 16 <= tc::MAX_NH);
+    const bool ok = rotate_tc_fits(k, m) || (k == m && !out1 && m >= 1);
     if (!ok) return fail(ctx, RSDFT_E_INVALID, "tensor-core rotation: k %d, m %d", k, m);
     tc::Buffers b;
     RS_TRY(tc::buffers(ctx, 0, 2 * k, b));   // the layout gram_tc_sh wrote: [Y; HY]

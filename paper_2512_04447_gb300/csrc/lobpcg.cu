@@ -308,6 +308,17 @@ __global__ void k_rq_fin(const double2 *__restrict__ part, int S, int m, double 
     theta[b] = s / q;
 }
 
+// g[m + j][i] = conj(g[i][m + j]) for i < m, j < nwp, in both matrices (ld k)
+__global__ void k_mirror_block(double2 *gs, double2 *gh, int k, int m, int nwp) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    for (int j = blockIdx.y * 32 + threadIdx.y; j < min(nwp, (int)(blockIdx.y + 1) * 32); j += blockDim.y) {
+        if (i >= m) continue;
+        const double2 a = gs[(size_t)i * k + m + j], b = gh[(size_t)i * k + m + j];
+        gs[(size_t)(m + j) * k + i] = make_double2(a.x, -a.y);
+        gh[(size_t)(m + j) * k + i] = make_double2(b.x, -b.y);
+    }
+}
+
 // out += in, FP32 values added to an FP64 block
 __global__ void k_add_f32(double2 *out, const float2 *__restrict__ in, long long cnt) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -618,24 +629,30 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
 }
 
 // FP64 refinement of the mixed form with FP32 corrections.  X and HX are FP64:
-// the residuals and their norms, T_b, the X-X blocks of G_S and G_H and the X
-// part of the Ritz rotation are formed in FP64.  The corrections W = TPA(R),
-// HW = H W and the directions P, HP stay on the FP32 data path, with the Gram
-// blocks that involve them (split-BF16 tensor cores when tensor_cores >= 1):
-//  - an error e in a block that couples X to W or P moves the Ritz values by
-//    O(e^2 / gap) and X by O(e |C_WP|), and the coefficients C_WP of the
-//    corrections fall with the residual; the X-X blocks, which move the Ritz
-//    values by O(e), are FP64;
+// the residuals and their norms, the X-X blocks of G_S and G_H, the blocks that
+// couple X to the corrections, and the X part of the Ritz rotation are formed in
+// FP64.  The corrections W = TPA(R), HW = H W and the directions P, HP are FP32,
+// and only the Gram blocks among them run on the FP32 path (split-BF16 tensor
+// cores when tensor_cores >= 1):
+//  - an error e in a coupling block would move the Ritz vectors by O(e / gap)
+//    whatever the residual, a floor at the FP32 level; so the couplings are
+//    FP64, G_S[X][W] = <X|W> and G_H[X][W] = <HX|W> from the FP64 X, HX and the
+//    stored FP32 rows (H Hermitian), which keeps them consistent with the W
+//    that the rotation uses whatever the rounding of HW;
+//  - an error e in a block among W and P moves the Ritz vectors by
+//    O(e |C_WP| / gap), and the coefficients C_WP fall with the residual;
 //  - R is formed in FP64 before it is rounded, so W keeps FP32 relative accuracy
 //    however small the residual is;
 //  - HP = H P is recomputed from the normalised P every iteration (carried by
 //    the rotation, its FP32 rounding would be relative to |p|, which falls with
 //    the residual), so no P column needs to leave the basis;
 //  - the FP64 residual norms certify the tolerance.
-// P and HP of the FP32 phase (carryP) seed the first iteration.
+// P and HP of the FP32 phase (carryP) seed the first iteration.  Three
+// iterations each gaining less than 10% set *stalled, and the caller continues
+// with the all-FP64 iteration.
 static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_opts &o, double stop_tol,
                                   int maxit, bool carryP, RunState &rs, double *hres, rsdft_lobpcg_stats *stats,
-                                  cudaStream_t st) {
+                                  bool *stalled, cudaStream_t st) {
     using B32 = RowBlocksT<float2>;
     Workspace &w = ctx->ws;
     const long long n = ctx->n;
@@ -668,7 +685,9 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
     PhaseEvents pe;
     if (stats) RS_TRY(pe.init(ctx));
     bool haveP = carryP;
-    int it = 0;
+    int it = 0, slow = 0;
+    double prev = -1.0;
+    *stalled = false;
     rsdft_status result = RSDFT_OK;
     for (;;) {
         RS_TRY(resid_norms<double2>(ctx, HX, X, m, st));
@@ -684,6 +703,12 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
         if (bad) { result = fail(ctx, RSDFT_E_NUMERIC, "non-finite residual at refinement iteration %d", it); break; }
         rs.converged = rmax <= stop_tol;
         if (rs.converged || it >= maxit) break;
+        // three iterations each gaining less than 10%: hand over to the FP64 iteration
+        if (prev > 0.0) {
+            slow = rmax > 0.9 * prev ? slow + 1 : 0;
+            if (slow >= 3) { *stalled = true; break; }
+        }
+        prev = rmax;
         int na = 0;
         for (int b = 0; b < m; ++b)
             if (hres[b] > lock_tol) hact[na++] = b;
@@ -755,16 +780,26 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[2], st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[3], st));
         const int k = m + na + np_;
-        // the X rows of HY enter only the X-X block of G_H, which is replaced
-        // by the FP64 block below: Xs stands in for them
-        B32 Y{{Xs, W, Pn}, {m, na, np_}};
-        B32 HY{{Xs, HW, HPn}, {m, na, np_}};
-        RS_TRY(gram_pair<float2>(ctx, Y, HY, w.GS, w.GH, k, tc, st));
+        const int nwp = na + np_;
+        // Gram blocks: [W P]-[W P] on the FP32 path; X-X and the X-[W P]
+        // couplings in FP64 (the latter from FP64 X and HX against the FP32 rows,
+        // G_H[X][W] = <HX|W>, consistent with the stored W whatever the rounding of HW)
         {
+            B32 Y{{W, Pn, nullptr}, {na, np_, 0}};
+            B32 HY{{HW, HPn, nullptr}, {na, np_, 0}};
+            // FP32 CUDA cores even with tensor_cores set: the split-BF16 error
+            // (1e-5 of max |G|) in these blocks, divided by small gaps of the
+            // projected problem, slowed the refinement below 1e-8
+            RS_TRY(gram_pair<float2>(ctx, Y, HY, w.GS + (size_t)m * k + m, w.GH + (size_t)m * k + m, k, false, st));
             RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
             RowBlocks HYX{{HX, nullptr, nullptr}, {m, 0, 0}};
             RS_TRY(gram(ctx, YX, YX, w.GS, k, true, dV, st));
             RS_TRY(gram(ctx, YX, HYX, w.GH, k, true, dV, st));
+            RS_TRY(gram64x32(ctx, YX, Y, w.GS + m, k, dV, st));
+            RS_TRY(gram64x32(ctx, HYX, Y, w.GH + m, k, dV, st));
+            k_mirror_block<<<dim3(cdiv(m, 32), cdiv(nwp, 32)), dim3(32, 8), 0, st>>>(w.GS, w.GH, k, m, nwp);
+            count_launch(ctx);
+            RS_LAUNCHED(ctx, "k_mirror_block");
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
         int nd = 0;
@@ -837,10 +872,19 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
         if (o.tol > 0.0 || rs.iterations < o.maxit) {
             RunState r2;
             const int left = o.tol > 0.0 ? std::max(0, o.maxit - rs.iterations) : o.maxit - rs.iterations;
+            bool stalled = false;
             if (o.refine == RSDFT_REFINE_FP32_CORRECTIONS)
-                r = lobpcg_refine(ctx, x, m, o, o.tol, left, rs.haveP, r2, hres, stats, st);
+                r = lobpcg_refine(ctx, x, m, o, o.tol, left, rs.haveP, r2, hres, stats, &stalled, st);
             else
                 r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
+            if (r == RSDFT_OK && stalled) {
+                RunState r3;
+                r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, std::max(0, left - r2.iterations), false, r3, hres,
+                                      stats, st);
+                r2.iterations += r3.iterations;
+                r2.dropped += r3.dropped;
+                r2.converged = r3.converged;
+            }
             rs.iterations += r2.iterations;
             rs.dropped += r2.dropped;
             rs.converged = r2.converged;
@@ -878,7 +922,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->precision = RSDFT_FP64;
     o->lock_tol = 1e-10;
     o->pivot_tol = 1e-8;
-    o->switch_tol = 1e-4;
+    o->switch_tol = 3e-5;
     o->tensor_cores = 0;
     o->learned_iters = 0;
     o->refine = RSDFT_REFINE_FP32_CORRECTIONS;

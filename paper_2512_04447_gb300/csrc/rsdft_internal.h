@@ -243,6 +243,9 @@ rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ld
 // partials reduced in FP64; rotation coefficients rounded to FP32.
 rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
                     double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st);
+// FP64 rows A against FP32 rows B (converted exactly, products and sums in FP64).
+rsdft_status gram64x32(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocksT<float2> &B, double2 *g, int ldg,
+                       double scale, cudaStream_t st);
 rsdft_status rotate32(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const double2 *c, int ldc, int m,
                       const float2 *base, int sign, float2 *out0, float2 *out1, cudaStream_t st);
 // Tensor-core (split-BF16, tcgen05) Grams of FP32 blocks (gram_tc.cu).
@@ -253,7 +256,8 @@ rsdft_status gram_tc(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlock
 // Ritz rotation on the tensor cores from the split-BF16 rows that the last
 // gram_tc_sh left in the workspace (which = 0: Y, which = 1: HY):
 // out0 = Y C (all k rows), out1 = Y[m:k] C[m:k] (the new P).  rotate_tc_fits
-// says whether the shape is supported (m <= 240).
+// says whether the shape is supported (k > m >= 1; more than 240 bands go in
+// groups of at most 240).
 bool rotate_tc_fits(int k, int m);
 rsdft_status rotate_tc_split(rsdft_ctx *ctx, int which, int k, const double2 *c, int ldc, int m,
                              float2 *out0, float2 *out1, cudaStream_t st);

@@ -111,7 +111,9 @@ ROT_TOL = 5e-5
 
 @pytest.mark.parametrize("N,k,m", [((24, 24, 24), 48, 16), ((20, 18, 15), 11, 5),
                                    ((24, 24, 24), 432, 144), ((16, 16, 16), 300, 144),
-                                   ((20, 18, 15), 100, 33)])
+                                   ((20, 18, 15), 100, 33),
+                                   # more bands than one accumulator pair: band groups
+                                   ((16, 16, 16), 900, 480), ((20, 18, 15), 500, 250)])
 def test_rotate_bf16x3_matches_fp64(N, k, m):
     ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
     y = draw_x0(11, k, ctx.n).astype(np.complex64)
@@ -132,7 +134,7 @@ def test_rotate_bf16x3_rejects_unsupported_shapes():
     N = (12, 12, 12)
     ctx = R.Context((5.0, 5.0, 5.0), N, np.zeros(N[0] * N[1] * N[2]))
     y = torch.zeros((300, ctx.n), dtype=torch.complex64, device="cuda")
-    for k, m in [(256, 256), (300, 250)]:
+    for k, m in [(256, 256), (250, 300)]:   # k must exceed m (out1 is the new P)
         c = torch.zeros((k, m), dtype=torch.complex128, device="cuda")
         o = torch.zeros((m, ctx.n), dtype=torch.complex64, device="cuda")
         with pytest.raises(R.RsdftError):
