@@ -496,6 +496,19 @@ def run_profile_case(case):
         r = torch.randn(16, ctx.n, dtype=torch.complex128, device="cuda", generator=g)
         w = torch.zeros_like(r)
         ctx.precond_learned(r, w, w)
+    elif case in ("tridiag", "dense"):
+        # the subspace solve of Eq. 1 at the bench's largest size, k = 432 (a 3 MB
+        # matrix: the full-size launch); tridiag runs the eigensolve alone
+        k = 432
+        a = torch.randn(k, k, dtype=torch.complex128, device="cuda", generator=g)
+        h = 0.5 * (a + a.conj().T)
+        if case == "tridiag":
+            z = torch.empty(k, k // 3, dtype=torch.complex128, device="cuda")
+            ctx.eigh(h, k // 3, z)
+        else:
+            gs = (a.conj().T @ a) / k + torch.eye(k, dtype=torch.complex128, device="cuda")
+            c = torch.empty(k, k // 3, dtype=torch.complex128, device="cuda")
+            ctx.rayleigh_ritz(h, gs, k // 3, c)
     elif case.startswith("hpsi"):
         x = torch.randn(16, ctx.n, dtype=cdt, device="cuda", generator=g)
         hx = torch.empty_like(x)
@@ -626,7 +639,13 @@ def micro_fft(R, torch, grids, batch, reps):
             nb = batch if batch * n * esz * 2 < 60e9 else max(1, int(60e9 // (n * esz * 2)))
             x = torch.randn(nb, n, dtype=dt, device="cuda", generator=g)
             hx = torch.empty_like(x)
-            t1 = _events_ms(torch, lambda: ctx.apply_h(x[:1], hx[:1], precision=prec), reps)
+            try:
+                t1 = _events_ms(torch, lambda: ctx.apply_h(x[:1], hx[:1], precision=prec), reps)
+            except R.RsdftError as err:   # e.g. an FP64 xy plane beyond shared memory
+                rec[name] = {"unsupported": str(err)}
+                del x, hx
+                torch.cuda.empty_cache()
+                continue
             tb = _events_ms(torch, lambda: ctx.apply_h(x, hx, precision=prec), max(1, reps // 4))
             per = tb / nb
             rec[name] = {"batch": nb, "ms_per_band_single": t1, "ms_per_band_batched": per,
@@ -980,7 +999,8 @@ def main():
     ap.add_argument("--group", type=int, default=8, help="batched: cells per group (device memory)")
     ap.add_argument("--concurrent", type=int, default=8, help="batched: cells in flight")
     ap.add_argument("--profile-case", default=None,
-                    help="run one small case for ncu (gram, gram_tc, rotate, rotate_tc, hpsi, hpsi32, nn_conv) "
+                    help="run one small case for ncu (gram, gram_tc, rotate, rotate_tc, hpsi, hpsi32, nn_conv, "
+                         "tridiag, dense) "
                          "and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -252,8 +252,10 @@ typedef struct {
                               blocks of G_S and G_H, the X part of the rotation)
                               and forms W = TPA(R), H W, P, H P and the Gram blocks
                               that involve them on the FP32 path (recomputing H P
-                              each iteration; three iterations each gaining less
-                              than 10% hand over to the FP64 iterations);
+                              each iteration) down to a residual of 1e-8; FP64
+                              iterations finish tighter tolerances, and take over
+                              when it stalls (three iterations each gaining less
+                              than 10%, or a residual ten times its best);
                               RSDFT_REFINE_FP64 runs them all in FP64.  Both stop
                               on the FP64 residual norms.                         */
 } rsdft_lobpcg_opts;

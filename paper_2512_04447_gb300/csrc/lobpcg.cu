@@ -34,6 +34,10 @@ constexpr double LOCK_TOL_FP32 = 1e-6;
 // FP32 run diverged with a 3e-6 threshold and stayed at 5e-8 Ha with 1e-5; 1e-4
 // keeps a factor 10 of margin while leaving unconverged bands their P.
 constexpr double P_DROP_FP32 = 1e-4;
+// Lowest residual the refinement with FP32 corrections is asked for; tighter
+// tolerances are finished by FP64 iterations (a 1e-10 request otherwise ran
+// 288 iterations on the 64^3 cell's fourth SCF step and diverged).
+constexpr double REFINE32_FLOOR = 1e-8;
 
 __device__ __forceinline__ double block_sum2(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -686,7 +690,7 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
     if (stats) RS_TRY(pe.init(ctx));
     bool haveP = carryP;
     int it = 0, slow = 0;
-    double prev = -1.0;
+    double prev = -1.0, best = -1.0;
     *stalled = false;
     rsdft_status result = RSDFT_OK;
     for (;;) {
@@ -703,12 +707,14 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
         if (bad) { result = fail(ctx, RSDFT_E_NUMERIC, "non-finite residual at refinement iteration %d", it); break; }
         rs.converged = rmax <= stop_tol;
         if (rs.converged || it >= maxit) break;
-        // three iterations each gaining less than 10%: hand over to the FP64 iteration
+        // three iterations each gaining less than 10%, or a residual ten times its
+        // best so far: hand over to the FP64 iteration
         if (prev > 0.0) {
             slow = rmax > 0.9 * prev ? slow + 1 : 0;
-            if (slow >= 3) { *stalled = true; break; }
+            if (slow >= 3 || rmax > 10.0 * best) { *stalled = true; break; }
         }
         prev = rmax;
+        best = best > 0.0 ? std::min(best, rmax) : rmax;
         int na = 0;
         for (int b = 0; b < m; ++b)
             if (hres[b] > lock_tol) hact[na++] = b;
@@ -873,10 +879,18 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
             RunState r2;
             const int left = o.tol > 0.0 ? std::max(0, o.maxit - rs.iterations) : o.maxit - rs.iterations;
             bool stalled = false;
-            if (o.refine == RSDFT_REFINE_FP32_CORRECTIONS)
-                r = lobpcg_refine(ctx, x, m, o, o.tol, left, rs.haveP, r2, hres, stats, &stalled, st);
-            else
+            if (o.refine == RSDFT_REFINE_FP32_CORRECTIONS) {
+                // the FP32 blocks among the corrections bound what this refinement
+                // reaches (their errors, ~eps32 |H|, enter the Ritz vectors scaled by
+                // the residual over the squared gap of the projected problem): it
+                // runs to REFINE32_FLOOR, the FP64 iteration finishes below
+                r = lobpcg_refine(ctx, x, m, o, std::max(o.tol, REFINE32_FLOOR), left, rs.haveP, r2, hres, stats,
+                                  &stalled, st);
+                if (r == RSDFT_OK && !r2.converged && !stalled && r2.iterations < left) stalled = true;
+                if (r == RSDFT_OK && r2.converged && o.tol < REFINE32_FLOOR) stalled = true;
+            } else {
                 r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
+            }
             if (r == RSDFT_OK && stalled) {
                 RunState r3;
                 r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, std::max(0, left - r2.iterations), false, r3, hres,
