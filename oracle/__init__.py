@@ -19,6 +19,8 @@ checked against the paper by eye:
 * ``precond``     -- the learned preconditioner: a residual-form periodic 3D
                      convolutional network on TPA, its gradient, Adam, and the
                      projected correction targets by MINRES
+* ``tddft``       -- real-time propagation by the Taylor series of exp(-i H dt)
+* ``gga``         -- PBE exchange-correlation (the paper's functional), FFT gradients
 * ``scf``         -- density, FFT Hartree, LDA (Slater + Perdew-Zunger 1981),
                      occupations (aufbau / Fermi-Dirac), Anderson mixing, and
                      one SCF step (the "Others" component of Fig. 1)

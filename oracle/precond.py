@@ -35,8 +35,13 @@ gives no network; the readings used here and in the CUDA path are:
   (Kingma and Ba 2015, Algorithm 1: beta1 0.9, beta2 0.999, eps 1e-8) on
   mini-batches taken in cyclic order (batch k = samples k B .. k B + B - 1
   modulo the sample count).
-* Target: t_b solves (I - x x^H)(H - e_b)(I - x x^H) t = -r_b, t perpendicular
-  to x_b, by MINRES (Paige and Saunders 1975) to a relative residual of 1e-3;
+* Target: t_b solves Q (H - e_b) Q t = -Q r_b with Q = I - X X^H the projector
+  off the whole block X (t perpendicular to every x_c), by MINRES (Paige and
+  Saunders 1975) to a relative residual of 1e-3.  Projecting off x_b alone left
+  (H - e_b)^-1 to amplify the components along the other bands of the block
+  whose eigenvalues lie near e_b: those dominate the single-band target, the
+  network learned them, and LOBPCG, which removes span(X) from W, was left with
+  the small rest (a stall at the initial residual level on both judged cells);
   LOBPCG uses only the direction of a preconditioned residual, so the target
   plane is t_b rescaled to the norm of TPA(r_b), with the sign that makes it
   point along TPA(r_b): y = c_b t_b / s_b, c_b = sign(Re<t_b|TPA(r_b)>)
@@ -278,13 +283,15 @@ def minres(apply_a, b: np.ndarray, rtol: float = MINRES_RTOL, maxit: int = 500):
     return x, hist
 
 
-def correction_target(ham, x: np.ndarray, eps: float, r: np.ndarray, rtol: float = MINRES_RTOL,
+def correction_target(ham, X: np.ndarray, eps: float, r: np.ndarray, rtol: float = MINRES_RTOL,
                       maxit: int = 500):
-    """t perpendicular to x with (I - x x^H)(H - eps)(I - x x^H) t = -r (x normalised in the dV metric)."""
+    """t perpendicular to the block X with Q (H - eps) Q t = -Q r, Q = I - X X^H
+    (X [m][n] orthonormal in the dV metric; a single band is a block of one)."""
     dV = ham.dV
+    X = np.atleast_2d(X)
 
     def proj(z):
-        return z - x * (np.vdot(x, z) * dV)
+        return z - (X.conj() @ z * dV) @ X
 
     def op(z):
         pz = proj(z)
@@ -311,7 +318,7 @@ def training_planes(ham, X: np.ndarray, tpa_apply, rtol: float = MINRES_RTOL, ma
     base = tpa_apply(R)
     T = np.zeros_like(R)
     for i in range(X.shape[0]):
-        T[i], _ = correction_target(ham, X[i], e[i], R[i], rtol, maxit)
+        T[i], _ = correction_target(ham, X, e[i], R[i], rtol, maxit)
     tt = np.real(np.sum(T.conj() * T, axis=1))
     bb = np.real(np.sum(base.conj() * base, axis=1))
     tb = np.real(np.sum(T.conj() * base, axis=1))

@@ -53,6 +53,7 @@ import numpy as np
 import scipy.fft as sfft
 from scipy.special import expit
 
+from .gga import pbe_xc
 from .grid import Grid
 from .hamiltonian import Hamiltonian
 from .lobpcg import LobpcgResult, lobpcg
@@ -201,9 +202,14 @@ class ScfOut:
     lobpcg: LobpcgResult
 
 
-def effective_potential(grid: Grid, v_loc: np.ndarray, rho: np.ndarray):
+def effective_potential(grid: Grid, v_loc: np.ndarray, rho: np.ndarray, xc: str = "lda"):
     vh = hartree(grid, rho)
-    eps, vxc = lda_xc(rho)
+    if xc == "pbe":
+        eps, vxc = pbe_xc(grid, rho)
+    elif xc == "lda":
+        eps, vxc = lda_xc(rho)
+    else:
+        raise ValueError(xc)
     return v_loc + vh + vxc, vh, eps, vxc
 
 
@@ -216,7 +222,7 @@ def scf_init(grid: Grid, n_electrons: float, X0: np.ndarray, beta=0.3, depth=4) 
 
 def scf_step(ham: Hamiltonian, v_loc: np.ndarray, state: ScfState, n_electrons: float,
              kT: float, k_lobpcg: int = 3, first_maxit: int = 200, tol: float = 1e-6,
-             precond: str = "tpa", later_tol: float = 0.0) -> ScfOut:
+             precond: str = "tpa", later_tol: float = 0.0, xc: str = "lda") -> ScfOut:
     """One SCF step.  The first step converges LOBPCG to ``tol``; later steps
     run ``k_lobpcg`` iterations, or, with ``later_tol > 0``, also converge to
     ``later_tol`` (at most ``first_maxit`` iterations), which makes each step a
@@ -224,7 +230,7 @@ def scf_step(ham: Hamiltonian, v_loc: np.ndarray, state: ScfState, n_electrons: 
     path)."""
     grid = ham.grid
     dV = grid.dV
-    v_eff, vh, eps_xc, vxc = effective_potential(grid, v_loc, state.rho_in)
+    v_eff, vh, eps_xc, vxc = effective_potential(grid, v_loc, state.rho_in, xc)
     ham.set_potential(v_eff)
     m = state.X.shape[0]
     nocc = int(min(m, np.ceil(n_electrons / 2.0))) if kT <= 0 else m

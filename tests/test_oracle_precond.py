@@ -181,18 +181,22 @@ def test_correction_target_on_a_dense_6cubed_hamiltonian():
     H = hamiltonian_dense(g.N, g.L, ham.v, proj.B.toarray(), proj.E)
     dV = g.dV
     res = lobpcg(ham, draw_x0(4, 4, g.n), maxit=2)
-    x = res.X[2]
+    X = res.X
+    x = X[2]
     e = float(np.real(np.vdot(x, ham.apply(x[None])[0])) * dV)
     r = ham.apply(x[None])[0] - e * x
-    t, hist = P.correction_target(ham, x, e, r, rtol=1e-12, maxit=2000)
-    # dense: solve the projected system in the orthogonal complement of x
-    xn = x * np.sqrt(dV)                       # unit vector in the plain metric
-    Pm = np.eye(g.n) - np.outer(xn, xn.conj())
-    A = Pm @ (H - e * np.eye(g.n)) @ Pm
-    ref, *_ = np.linalg.lstsq(A, -(Pm @ r), rcond=None)
-    ref = Pm @ ref
-    assert abs(np.vdot(x, t) * dV) < 1e-10 * np.linalg.norm(t)
-    assert np.linalg.norm(t - ref) <= 1e-8 * np.linalg.norm(ref)
+    # dense: solve the projected system in the orthogonal complement of the block
+    Xn = X * np.sqrt(dV)                       # orthonormal rows in the plain metric
+    for block in (X, x):                        # the whole block, and x alone
+        Bn = np.atleast_2d(block) * np.sqrt(dV)
+        t, hist = P.correction_target(ham, block, e, r, rtol=1e-12, maxit=2000)
+        Pm = np.eye(g.n) - Bn.T @ Bn.conj()
+        A = Pm @ (H - e * np.eye(g.n)) @ Pm
+        ref, *_ = np.linalg.lstsq(A, -(Pm @ r), rcond=None)
+        ref = Pm @ ref
+        assert np.max(np.abs(np.atleast_2d(block).conj() @ t * dV)) < 1e-10 * np.linalg.norm(t)
+        assert np.linalg.norm(t - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.allclose(Xn.conj() @ Xn.T, np.eye(4), atol=1e-12)
 
 
 def test_training_planes_and_learned_apply():
@@ -214,7 +218,7 @@ def test_training_planes_and_learned_apply():
     for i in range(4):
         assert abs(np.linalg.norm(Yc[i]) - np.linalg.norm(Bc[i])) <= 1e-12 * np.linalg.norm(Bc[i])
         assert np.real(np.vdot(Yc[i], Bc[i])) >= 0.0
-        t, _ = P.correction_target(ham, X[i], ea[i], Ra[i], maxit=300)
+        t, _ = P.correction_target(ham, X, ea[i], Ra[i], maxit=300)
         cosang = abs(np.vdot(t, Yc[i])) / (np.linalg.norm(t) * np.linalg.norm(Yc[i]))
         assert abs(cosang - 1.0) < 1e-12
     # learned_apply with zero weights is the TPA base itself
