@@ -215,6 +215,12 @@ rsdft_status rsdft_rayleigh_ritz(rsdft_ctx *ctx, const void *gh_dev, const void 
 rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, double *lam_host,
                         void *z_dev, void *stream);
 
+/* Arithmetic of the tridiagonalisation inside rsdft_eigh and
+ * rsdft_rayleigh_ritz for this context: RSDFT_DENSE_FP64 (default; AUTO means
+ * the same here) or RSDFT_DENSE_DF (as rsdft_lobpcg_opts.dense).
+ * RSDFT_E_INVALID for another value. */
+rsdft_status rsdft_set_dense(rsdft_ctx *ctx, int mode);
+
 /* ---------------------------------------------------------------------------
  * LOBPCG for the lowest nband eigenpairs of H (the paper's eigensolver,
  * Knyazev's block method with the Rayleigh-Ritz of Eq. 1).  RSDFT_FP64 keeps
@@ -252,15 +258,24 @@ typedef struct {
                               blocks of G_S and G_H, the X part of the rotation)
                               and forms W = TPA(R), H W, P, H P and the Gram blocks
                               that involve them on the FP32 path (recomputing H P
-                              each iteration) down to a residual of 1e-8; FP64
-                              iterations finish tighter tolerances, and take over
+                              each iteration) down to a residual of 1e-7 (30
+                              iterations at most); FP64 iterations finish tighter
+                              tolerances, and take over
                               when it stalls (three iterations each gaining less
                               than 10%, or a residual ten times its best);
                               RSDFT_REFINE_FP64 runs them all in FP64.  Both stop
                               on the FP64 residual norms.                         */
+    int dense;             /* arithmetic of the Householder tridiagonalisation in
+                              the subspace eigensolve: RSDFT_DENSE_AUTO (default)
+                              = double-float in RSDFT_MIXED, FP64 in RSDFT_FP64;
+                              RSDFT_DENSE_FP64; RSDFT_DENSE_DF = double-float
+                              (FP32 pairs, ~2^-46 relative per operation) on one
+                              16-CTA thread-block cluster with the matrix in its
+                              shared memory, for subspaces up to 448 (FP64 above) */
 } rsdft_lobpcg_opts;
 
 enum { RSDFT_REFINE_FP64 = 0, RSDFT_REFINE_FP32_CORRECTIONS = 1 };
+enum { RSDFT_DENSE_AUTO = 0, RSDFT_DENSE_FP64 = 1, RSDFT_DENSE_DF = 2 };
 
 typedef struct {
     int iterations;        /* full iterations done (both phases)                   */
@@ -331,7 +346,10 @@ typedef struct {
                               later_tol (at most first_maxit iterations; the mixed
                               form as in the first solve), so that each step is a
                               function of rho_in alone                            */
+    int xc;                /* RSDFT_XC_LDA (default) or RSDFT_XC_PBE               */
 } rsdft_scf_opts;
+
+enum { RSDFT_XC_LDA = 0, RSDFT_XC_PBE = 1 };
 
 typedef struct {
     double e_tot;          /* sum f eps - E_H - int v_xc rho + E_xc (at rho_in)    */
@@ -358,6 +376,13 @@ rsdft_status rsdft_density(rsdft_ctx *ctx, const void *x_dev, const double *f_de
 rsdft_status rsdft_hartree(rsdft_ctx *ctx, const double *rho_dev, double *vh_dev, void *stream);
 rsdft_status rsdft_lda(rsdft_ctx *ctx, const double *rho_dev, double *eps_dev, double *vxc_dev,
                        void *stream);
+/* GGA exchange-correlation of Perdew, Burke and Ernzerhof (PBE, the paper's
+ * functional), spin-unpolarised, with PW92 correlation of the uniform gas:
+ * eps_dev = e / rho and vxc_dev = de/drho - div(2 de/dsigma grad rho) for
+ * e(rho, sigma = |grad rho|^2); gradients and the divergence by FFT (i G_a,
+ * the Nyquist plane of an even axis set to zero); points with rho < 1e-12
+ * contribute nothing.  [n] doubles on the device. */
+rsdft_status rsdft_xc_pbe(rsdft_ctx *ctx, const double *rho_dev, double *eps_dev, double *vxc_dev, void *stream);
 /* Occupations on the device: eig_dev [nband] ascending -> f_dev [nband];
  * mu_host, entropy_host may be NULL. */
 rsdft_status rsdft_occupations(rsdft_ctx *ctx, const double *eig_dev, int nband,
@@ -365,6 +390,19 @@ rsdft_status rsdft_occupations(rsdft_ctx *ctx, const double *eig_dev, int nband,
                                double *entropy_host, void *stream);
 /* Density rho_in as held by the SCF state (device, [n]); NULL before init. */
 const double *rsdft_scf_density(const rsdft_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Real-time propagation (RS-TDDFT: i d psi/dt = H psi, the application the
+ * paper's real-space code serves, in its introduction), V held fixed:
+ * nsteps steps of psi <- sum_{j=0}^{order} (-i dt H)^j / j! psi, the truncated
+ * Taylor series of exp(-i H dt), each term one batched H psi (FP64).
+ * psi_dev: [nband][n] complex128, device, in/out.  1 <= order <= 16,
+ * nsteps >= 0, dt finite (Ha^-1 time units), else RSDFT_E_INVALID.  Uses the
+ * context's workspace (no allocation after the first call for nband bands).
+ * Asynchronous on the stream.
+ */
+rsdft_status rsdft_propagate(rsdft_ctx *ctx, void *psi_dev, int nband, double dt, int nsteps, int order,
+                             void *stream);
 
 /* ---------------------------------------------------------------------------
  * Per-kernel timing (the per-component breakdown of Fig. 1, finer grained).
@@ -447,8 +485,9 @@ rsdft_status rsdft_precond_learned(rsdft_ctx *ctx, const void *r_dev, const void
 /* Training samples from a block of normalised approximate orbitals x_dev
  * ([nband][n] complex128, e.g. LOBPCG iterates): per band e = <x|H|x>,
  * r = H x - e x, s = sqrt(sum |r|^2 / n), base = TPA(r) (T_b = <x|T|x>), and
- * t perpendicular to x solving (I - x x^H)(H - e)(I - x x^H) t = -r by MINRES
- * (Paige-Saunders) to relative residual rtol or maxit iterations (FP64);
+ * t perpendicular to the whole block solving Q (H - e) Q t = -Q r, Q = I - X X^H
+ * with X all nband orbitals (orthonormal), by MINRES (Paige-Saunders) to
+ * relative residual rtol or maxit iterations (FP64);
  * c = sign(Re<t|base>) ||base|| / ||t|| (t rescaled to the TPA norm, pointing
  * along it: LOBPCG uses only the direction).  Writes float planes
  * [2 nband][n] (real parts of every band, then imaginary parts): u = r / s,

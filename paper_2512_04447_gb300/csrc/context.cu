@@ -106,16 +106,21 @@ static rsdft_status build_fft_tables(rsdft_ctx *ctx) {
             tw[k] = make_double2(c, s);
             twf[k] = make_float2((float)c, (float)s);
         }
-        std::vector<double> g2(N);
+        std::vector<double> g2(N), g1(N);
         double gunit = 2.0 * M_PI / ctx->L[a];
         for (int pos = 0; pos < N; ++pos) {
             int k = position_to_freq(p, pos);
             int ks = k < (N + 1) / 2 ? k : k - N;
             double g = gunit * ks;
             g2[pos] = g * g;
+            // first derivatives: the Nyquist plane of an even axis gets 0 (for a
+            // real field its derivative is imaginary, i.e. 0 in the real part)
+            g1[pos] = (N % 2 == 0 && k == N / 2) ? 0.0 : g;
         }
         std::vector<float> g2f(g2.begin(), g2.end());
-        double2 *d_tw; float2 *d_twf; double *d_g2; float *d_g2f;
+        double2 *d_tw; float2 *d_twf; double *d_g2; float *d_g2f; double *d_g1;
+        RS_TRY(upload(ctx, &d_g1, g1.data(), N));
+        ctx->fft.gpos[a] = d_g1;
         RS_TRY(upload(ctx, &d_tw, tw.data(), N));
         RS_TRY(upload(ctx, &d_twf, twf.data(), N));
         RS_TRY(upload(ctx, &d_g2, g2.data(), N));

@@ -1198,7 +1198,7 @@ k_backtransform_wy(int k, const double2 *__restrict__ vh, int ldv, const double2
 }
 
 rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
-                         double2 *z, int ldz, cudaStream_t st) {
+                         double2 *z, int ldz, cudaStream_t st, bool df) {
     Workspace &w = ctx->ws;
     if (k <= 0 || nkeep <= 0) return RSDFT_OK;
     if (k > w.cap_k) return fail(ctx, RSDFT_E_INVALID, "subspace %d exceeds workspace %d", k, w.cap_k);
@@ -1215,8 +1215,10 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
     const double kd = (double)k;
     {
         ProfScope ps(ctx, RSDFT_K_TRIDIAG, 16.0 / 3.0 * kd * kd * kd, 0.0, st, 0);
-        // one cooperative launch for all Householder steps (occupancy queried once,
-        // thread-safe static initialisation)
+        bool cluster_done = false;
+        if (df) RS_TRY(tridiag_cluster(ctx, a, k, ld, w.Vh, k, w.tau, w.d, w.e, st, &cluster_done));
+        // else one cooperative launch for all Householder steps (occupancy queried
+        // once, thread-safe static initialisation)
         static const int occ = [] {
             int dev = 0, coop = 0, o = 0;
             cudaGetDevice(&dev);
@@ -1235,8 +1237,10 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         // cooperative grids of different contexts (batched cells on other streams)
         // never run at the same time: the lock is held until this call's final
         // stream synchronisation
-        if (occ > 0 && k <= MAX_K_COOP) coop_lock = std::unique_lock<std::mutex>(coop_mutex());
-        if (occ > 0 && k <= MAX_K_COOP) {
+        if (cluster_done) coop_done = true;
+        const bool try_coop = !cluster_done && occ > 0 && k <= MAX_K_COOP;
+        if (try_coop) coop_lock = std::unique_lock<std::mutex>(coop_mutex());
+        if (try_coop) {
             int nb = std::max(1, std::min(ctx->num_sms * std::min(occ, 1), cdiv((long long)k * k, 1024)));
             GridSync *gs = reinterpret_cast<GridSync *>(w.gsync);
             RS_CUDA(ctx, cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
@@ -1322,7 +1326,7 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         count_launch(ctx);
     }
     RS_LAUNCHED(ctx, "tridiagonal eigensolve");
-    if (coop_done) {
+    if (coop_lock.owns_lock()) {
         // a barrier wait of the cooperative kernel that gave up leaves err set
         int *slot = reinterpret_cast<int *>(w.hbuf + w.hbuf_elems - 16);
         RS_CUDA(ctx, cudaMemcpyAsync(slot, &reinterpret_cast<GridSync *>(w.gsync)->err, sizeof(int),
@@ -1407,7 +1411,7 @@ __global__ void k_place_rows(const double2 *__restrict__ cc, int kc, int ncol,
 
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,
                            int nkeep, double pivot_tol, double *lam_dev, double2 *c_out,
-                           int *ndropped, cudaStream_t st) {
+                           int *ndropped, cudaStream_t st, bool df) {
     Workspace &w = ctx->ws;
     if (k > w.cap_k) return fail(ctx, RSDFT_E_INVALID, "subspace %d exceeds workspace %d", k, w.cap_k);
     if (nkeep > k || nkeep <= 0) return fail(ctx, RSDFT_E_INVALID, "bad nkeep");
@@ -1459,7 +1463,7 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     count_launch(ctx);
     RS_LAUNCHED(ctx, "reduction");
     // eigenpairs of K (destroys Ym; the reflectors overwrite Vh)
-    RS_TRY(eigh_lowest(ctx, w.Ym, kc, nkeep, lam_dev, w.Zc, nkeep, st));
+    RS_TRY(eigh_lowest(ctx, w.Ym, kc, nkeep, lam_dev, w.Zc, nkeep, st, df));
     // C = L^-H Z
     {
         ProfScope pt(ctx, RSDFT_K_TRSM, 4.0 * kcd * kcd * nkeep, 0.0, st, 0);
@@ -1488,7 +1492,7 @@ rsdft_status rsdft_rayleigh_ritz(rsdft_ctx *ctx, const void *gh_dev, const void 
     cudaStream_t st = as_stream(stream);
     int nd = 0;
     RS_TRY(rayleigh_ritz(ctx, (const double2 *)gh_dev, (const double2 *)gs_dev, k, nkeep, pivot_tol,
-                         ctx->ws.lam, (double2 *)c_dev, &nd, st));
+                         ctx->ws.lam, (double2 *)c_dev, &nd, st, ctx->dense_mode == RSDFT_DENSE_DF));
     RS_CUDA(ctx, cudaMemcpyAsync(lam_host, ctx->ws.lam, nkeep * sizeof(double), cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaStreamSynchronize(st));
     if (ndropped_host) *ndropped_host = nd;
@@ -1504,9 +1508,18 @@ rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, dou
     cudaStream_t st = as_stream(stream);
     RS_CUDA(ctx, cudaMemcpyAsync(ctx->ws.Ym, a_dev, (size_t)k * k * sizeof(double2),
                                  cudaMemcpyDeviceToDevice, st));
-    RS_TRY(eigh_lowest(ctx, ctx->ws.Ym, k, nkeep, ctx->ws.lam, (double2 *)z_dev, nkeep, st));
+    RS_TRY(eigh_lowest(ctx, ctx->ws.Ym, k, nkeep, ctx->ws.lam, (double2 *)z_dev, nkeep, st,
+                       ctx->dense_mode == RSDFT_DENSE_DF));
     RS_CUDA(ctx, cudaMemcpyAsync(lam_host, ctx->ws.lam, nkeep * sizeof(double), cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaStreamSynchronize(st));
+    return RSDFT_OK;
+}
+
+rsdft_status rsdft_set_dense(rsdft_ctx *ctx, int mode) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (mode != RSDFT_DENSE_AUTO && mode != RSDFT_DENSE_FP64 && mode != RSDFT_DENSE_DF)
+        return fail(ctx, RSDFT_E_INVALID, "unknown dense mode %d", mode);
+    ctx->dense_mode = mode;
     return RSDFT_OK;
 }
 

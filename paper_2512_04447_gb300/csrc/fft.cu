@@ -194,6 +194,7 @@ template <typename V> struct FftTabs {
     AxisPlan ax[3];
     const V *tw[3];
     const typename Sc<V>::T *g2[3];
+    const double *g1[3];   // G_a (first derivatives; FP64 real fields only)
     double inv_n;   // 1 / (Nx Ny Nz), formed on the host
 };
 
@@ -203,6 +204,7 @@ static FftTabs<double2> tabs_of(const rsdft_ctx *ctx, double2 *) {
         t.ax[a] = ctx->fft.ax[a];
         t.tw[a] = ctx->fft.tw64[a];
         t.g2[a] = ctx->fft.g2pos[a];
+        t.g1[a] = ctx->fft.gpos[a];
     }
     t.inv_n = 1.0 / (double)ctx->n;
     return t;
@@ -213,6 +215,7 @@ static FftTabs<float2> tabs_of(const rsdft_ctx *ctx, float2 *) {
         t.ax[a] = ctx->fft.ax[a];
         t.tw[a] = ctx->fft.tw32[a];
         t.g2[a] = ctx->fft.g2pos32[a];
+        t.g1[a] = ctx->fft.gpos[a];
     }
     t.inv_n = 1.0 / (double)ctx->n;
     return t;
@@ -294,21 +297,37 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
         if (!(t >= 1e-12)) t = 1.0;
         tk = (T)t;
     }
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
-        T g2 = tb.g2[0][x] + gy2 + tb.g2[2][z];
-        T f;
-        if (MID == Mid::Kinetic) f = (T)0.5 * g2 * inv_n;
-        else if (MID == Mid::Tpa) f = tpa_k<T>((T)0.5 * g2 / tk) * inv_n;
-        else if (MID == Mid::Hartree) f = g2 > (T)0 ? (T)(4.0 * M_PI) / g2 * inv_n : (T)0;
-        else f = inv_n;
-        s_slab[i] = mk<V>(s_slab[i].x * f, s_slab[i].y * f);
-    }
-    __syncthreads();
-    fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
-        base[z * zstride + x] = s_slab[i];
+    if constexpr (MID == Mid::GradX || MID == Mid::GradY || MID == Mid::GradZ) {
+        // i G_a / n: (re, im) -> (-f im, f re)
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
+            const T ga = (T)(MID == Mid::GradX ? tb.g1[0][x] : (MID == Mid::GradY ? tb.g1[1][y] : tb.g1[2][z]));
+            const T f = ga * inv_n;
+            s_slab[i] = mk<V>(-f * s_slab[i].y, f * s_slab[i].x);
+        }
+        __syncthreads();
+        fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
+            base[z * zstride + x] = s_slab[i];
+        }
+    } else {
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
+            T g2 = tb.g2[0][x] + gy2 + tb.g2[2][z];
+            T f;
+            if (MID == Mid::Kinetic) f = (T)0.5 * g2 * inv_n;
+            else if (MID == Mid::Tpa) f = tpa_k<T>((T)0.5 * g2 / tk) * inv_n;
+            else if (MID == Mid::Hartree) f = g2 > (T)0 ? (T)(4.0 * M_PI) / g2 * inv_n : (T)0;
+            else f = inv_n;
+            s_slab[i] = mk<V>(s_slab[i].x * f, s_slab[i].y * f);
+        }
+        __syncthreads();
+        fft_lines<V, true>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
+            base[z * zstride + x] = s_slab[i];
+        }
     }
 }
 
@@ -535,6 +554,18 @@ rsdft_status fft_z_mid_t(rsdft_ctx *ctx, Mid mid, V *buf, const double *tkin, in
         case Mid::Scale:
             RS_TRY(set_smem(ctx, k_z_mid<V, Mid::Scale>, sm));
             k_z_mid<V, Mid::Scale><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
+            break;
+        case Mid::GradX:
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::GradX>, sm));
+            k_z_mid<V, Mid::GradX><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
+            break;
+        case Mid::GradY:
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::GradY>, sm));
+            k_z_mid<V, Mid::GradY><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
+            break;
+        case Mid::GradZ:
+            RS_TRY(set_smem(ctx, k_z_mid<V, Mid::GradZ>, sm));
+            k_z_mid<V, Mid::GradZ><<<grid, FFT_THREADS, sm, st>>>(tb, buf, tkin);
             break;
     }
     RS_LAUNCHED(ctx, "k_z_mid");

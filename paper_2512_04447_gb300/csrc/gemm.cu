@@ -37,11 +37,9 @@ __device__ __forceinline__ void upper_tile(int t, int T, int &ti, int &tj) {
 // mixed form: FP32 products and accumulation inside the CTA); the partials are
 // stored in FP64 and reduced in FP64 by k_gram_reduce.  Output tile edge 16*P
 // (each of the 16 x 16 threads owns P x P entries).
-// VB is the type of B's rows: V, or float2 with V = double2 (FP32 rows against
-// FP64 rows, converted exactly and multiplied in FP64).
-template <typename V, typename VB, int P>
+template <typename V, int P>
 __global__ void __launch_bounds__(GTHREADS)
-k_gram_partial(RowBlocksT<V> A, RowBlocksT<VB> B, int na, int nb, long long n, int hermitian, int Ti,
+k_gram_partial(RowBlocksT<V> A, RowBlocksT<V> B, int na, int nb, long long n, int hermitian, int Ti,
                int Tj, long long kchunk, double2 *__restrict__ part) {
     using T = decltype(V{}.x);
     constexpr int TE = 16 * P;
@@ -71,11 +69,7 @@ k_gram_partial(RowBlocksT<V> A, RowBlocksT<VB> B, int na, int nb, long long n, i
             va.x = va.y = vb.x = vb.y = (T)0;
             if (kk < k1) {
                 if (i0 + lrow < na) va = row_of(A, i0 + lrow, n)[kk];
-                if (j0 + lrow < nb) {
-                    const VB t = row_of(B, j0 + lrow, n)[kk];
-                    vb.x = (T)t.x;
-                    vb.y = (T)t.y;
-                }
+                if (j0 + lrow < nb) vb = row_of(B, j0 + lrow, n)[kk];
             }
             As[lk][lrow] = va;
             Bs[lk][lrow] = vb;
@@ -158,6 +152,18 @@ static rsdft_status ensure_gram_part(rsdft_ctx *ctx, size_t elems) {
     return RSDFT_OK;
 }
 
+rsdft_status ensure_gram_partials(rsdft_ctx *ctx, size_t elems) { return ensure_gram_part(ctx, elems); }
+
+rsdft_status gram_reduce(rsdft_ctx *ctx, int nsplit, int na, int nb, bool hermitian, int te, double scale,
+                         double2 *g, int ldg, cudaStream_t st) {
+    const long long tot = (long long)na * nb;
+    k_gram_reduce<<<cdiv(tot, 256), 256, 0, st>>>(ctx->ws.gram_part, nsplit, na, nb, hermitian ? 1 : 0, te, scale,
+                                                   g, ldg);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_gram_reduce");
+    return RSDFT_OK;
+}
+
 // Resident CTAs of a kernel per SM (queried once per instantiation).
 template <typename K> static int occupancy(K kernel, int threads) {
     int occ = 0;
@@ -197,12 +203,12 @@ static int pick_splits(int tiles, long long n, int capacity) {
     return best;
 }
 
-template <typename V, typename VB, int P>
-static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<VB> &B,
+template <typename V, int P>
+static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B,
                                 int na, int nb, double2 *g, int ldg, bool hermitian, double scale,
                                 cudaStream_t st) {
     constexpr int TE = 16 * P;
-    static int occ = occupancy(k_gram_partial<V, VB, P>, GTHREADS);
+    static int occ = occupancy(k_gram_partial<V, P>, GTHREADS);
     const int Ti = cdiv(na, TE), Tj = cdiv(nb, TE);
     const int tiles = hermitian ? Ti * (Ti + 1) / 2 : Ti * Tj;
     const long long n = ctx->n;
@@ -218,9 +224,9 @@ static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const Ro
                           (const void *)A.ptr[2] == (const void *)B.ptr[2];
         const double entries = hermitian ? 0.5 * na * (na + 1.0) : (double)na * nb;
         ProfScope ps(ctx, RSDFT_K_GRAM, 8.0 * (double)n * entries,
-                     (double)n * (same ? sizeof(V) * na : sizeof(V) * na + sizeof(VB) * nb), st);
-        k_gram_partial<V, VB, P><<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj,
-                                                            kchunk, ctx->ws.gram_part);
+                     (double)n * sizeof(V) * (same ? na : na + nb), st);
+        k_gram_partial<V, P><<<grid, GTHREADS, 0, st>>>(A, B, na, nb, n, hermitian ? 1 : 0, Ti, Tj, kchunk,
+                                                        ctx->ws.gram_part);
     }
     RS_LAUNCHED(ctx, "k_gram_partial");
     const long long tot = (long long)na * nb;
@@ -231,8 +237,8 @@ static rsdft_status gram_launch(rsdft_ctx *ctx, const RowBlocksT<V> &A, const Ro
     return RSDFT_OK;
 }
 
-template <typename V, typename VB = V>
-rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<VB> &B, double2 *g, int ldg,
+template <typename V>
+rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<V> &B, double2 *g, int ldg,
                     bool hermitian, double scale, cudaStream_t st) {
     const int na = A.cnt[0] + A.cnt[1] + A.cnt[2];
     const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
@@ -241,13 +247,13 @@ rsdft_status gram_t(rsdft_ctx *ctx, const RowBlocksT<V> &A, const RowBlocksT<VB>
     // tile edge 16 P, P in {2, 3, 4}: the least-padding rule, or the autotuner's pick
     auto run = [&](int c) -> rsdft_status {
         switch (c + 2) {
-            case 2: return gram_launch<V, VB, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-            case 3: return gram_launch<V, VB, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
-            default: return gram_launch<V, VB, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            case 2: return gram_launch<V, 2>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            case 3: return gram_launch<V, 3>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
+            default: return gram_launch<V, 4>(ctx, A, B, na, nb, g, ldg, hermitian, scale, st);
         }
     };
     // shapes in buckets of 32 (the subspace size changes as bands lock)
-    const std::string key = std::string(sizeof(V) == 8 ? "gram32 " : (sizeof(VB) == 8 ? "gram64x32 " : "gram64 ")) +
+    const std::string key = std::string(sizeof(V) == 8 ? "gram32 " : "gram64 ") +
                             std::to_string(cdiv(na, 32)) +
                             " " + std::to_string(cdiv(nb, 32)) + (hermitian ? " h" : " g");
     int chosen = 0;
@@ -262,10 +268,7 @@ rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocks
                     double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st) {
     return gram_t<float2>(ctx, A, B, g, ldg, hermitian, scale, st);
 }
-rsdft_status gram64x32(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocksT<float2> &B, double2 *g, int ldg,
-                       double scale, cudaStream_t st) {
-    return gram_t<double2, float2>(ctx, A, B, g, ldg, false, scale, st);
-}
+
 
 // ---- rotation ----------------------------------------------------------------------
 // Tile: 64 bands x 64 points.  Rows of Y are consumed block 1, block 2, then
@@ -488,7 +491,7 @@ rsdft_status rsdft_gram_static(const void *a_dev, int na, const void *b_dev, int
     RowBlocks B{{(const double2 *)b_dev, nullptr, nullptr}, {nb, 0, 0}};
     // every partial entry the reduction reads is written by this launch first,
     // so nothing left by an earlier call is read
-    k_gram_partial<double2, double2, 4><<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
+    k_gram_partial<double2, 4><<<dim3(tiles, nsplit), GTHREADS, 0, st>>>(A, B, na, nb, n, 0, Ti, Tj, kchunk, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, RSDFT_E_CUDA, "k_gram_partial: %s", cudaGetErrorString(e));
     k_gram_reduce<<<cdiv((long long)na * nb, 256), 256, 0, st>>>(part, nsplit, na, nb, 0, GT, scale,

@@ -35,9 +35,13 @@ constexpr double LOCK_TOL_FP32 = 1e-6;
 // keeps a factor 10 of margin while leaving unconverged bands their P.
 constexpr double P_DROP_FP32 = 1e-4;
 // Lowest residual the refinement with FP32 corrections is asked for; tighter
-// tolerances are finished by FP64 iterations (a 1e-10 request otherwise ran
-// 288 iterations on the 64^3 cell's fourth SCF step and diverged).
-constexpr double REFINE32_FLOOR = 1e-8;
+// tolerances are finished by FP64 iterations (asked for 1e-10, it ran 288
+// iterations on an SCF step of the 64^3 cell and diverged; the FP64-accurate
+// products of its couplings on the FP32 pipe carry ~2^-46 relative errors,
+// which over gaps of 1e-3 Ha reach the 1e-9 Ha residual level).  And at most
+// REFINE32_MAXIT of its iterations before the FP64 iteration takes over.
+constexpr double REFINE32_FLOOR = 1e-7;
+constexpr int REFINE32_MAXIT = 30;
 
 __device__ __forceinline__ double block_sum2(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -323,6 +327,23 @@ __global__ void k_mirror_block(double2 *gs, double2 *gh, int k, int m, int nwp) 
     }
 }
 
+// The m x m leading blocks of gs and gh (ld k) made Hermitian: the upper
+// triangle mirrored into the lower one, real diagonal.
+__global__ void k_herm_block(double2 *gs, double2 *gh, int k, int m) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    for (int j = blockIdx.y * 32 + threadIdx.y; j < min(m, (int)(blockIdx.y + 1) * 32); j += blockDim.y) {
+        if (i >= m || j > i) continue;
+        if (j == i) {
+            gs[(size_t)i * k + i].y = 0.0;
+            gh[(size_t)i * k + i].y = 0.0;
+            continue;
+        }
+        const double2 a = gs[(size_t)j * k + i], b = gh[(size_t)j * k + i];
+        gs[(size_t)i * k + j] = make_double2(a.x, -a.y);
+        gh[(size_t)i * k + j] = make_double2(b.x, -b.y);
+    }
+}
+
 // out += in, FP32 values added to an FP64 block
 __global__ void k_add_f32(double2 *out, const float2 *__restrict__ in, long long cnt) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -431,6 +452,11 @@ static rsdft_status gram_pair(rsdft_ctx *ctx, const RowBlocksT<V> &Y, const RowB
     return Ops<V>::gram(ctx, Y, HY, gh, k, true, ctx->dV, st);
 }
 
+// the double-float cluster tridiagonalisation in the subspace eigensolves
+static bool dense_df(const rsdft_lobpcg_opts &o) {
+    return o.dense == RSDFT_DENSE_DF || (o.dense == RSDFT_DENSE_AUTO && o.precision == RSDFT_MIXED);
+}
+
 struct RunState {
     int iterations = 0;
     int dropped = 0;
@@ -473,7 +499,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         Blocks HY{{HX, nullptr, nullptr}, {m, 0, 0}};
         RS_TRY(gram_pair(ctx, Y, HY, w.GS, w.GH, m, tc, st));
         int nd = 0;
-        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, pivot_tol, w.theta, w.Cfull, &nd, st));
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, m, m, pivot_tol, w.theta, w.Cfull, &nd, st, dense_df(o)));
         bool rotated = false;
         if constexpr (std::is_same<V, float2>::value) {
             if (tc_rot && rotate_tc_fits(m + 1, m)) {   // X-only rotation from the Gram's split rows
@@ -592,7 +618,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
         RS_TRY(gram_pair(ctx, Y, HY, w.GS, w.GH, k, tc, st));
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
         int nd = 0;
-        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st, dense_df(o)));
         rs.dropped += nd;
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[5], st));
         bool rotated = false;
@@ -634,8 +660,9 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
 
 // FP64 refinement of the mixed form with FP32 corrections.  X and HX are FP64:
 // the residuals and their norms, the X-X blocks of G_S and G_H, the blocks that
-// couple X to the corrections, and the X part of the Ritz rotation are formed in
-// FP64.  The corrections W = TPA(R), HW = H W and the directions P, HP are FP32,
+// couple X to the corrections, and the X part of the Ritz rotation are formed
+// to FP64 accuracy (the Grams and rotations on the FP32 pipe with error-free
+// products and compensated sums, gemm_df.cu).  The corrections W = TPA(R), HW = H W and the directions P, HP are FP32,
 // and only the Gram blocks among them run on the FP32 path (split-BF16 tensor
 // cores when tensor_cores >= 1):
 //  - an error e in a coupling block would move the Ritz vectors by O(e / gap)
@@ -666,6 +693,11 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
     float2 *W = (float2 *)w.W, *HW = (float2 *)w.HW, *P = (float2 *)w.P, *HP = (float2 *)w.HP;
     float2 *Pn = (float2 *)w.Pn, *HPn = (float2 *)w.HPn, *T1 = (float2 *)w.T1;
     float2 *Xs = w.Xs;
+    // lo parts of X and the pairs of HX in the unused halves of the FP64-sized
+    // buffers that hold FP32 rows here (T1: FFT scratch of at most m bands;
+    // Pn, HPn: at most m P columns)
+    const size_t mn = (size_t)m * ctx->n;
+    float2 *Xl = (float2 *)w.T1 + mn, *HXh = (float2 *)w.Pn + mn, *HXl = (float2 *)w.HPn + mn;
     float2 *proj = (float2 *)w.proj;
     int *hact = reinterpret_cast<int *>(w.hbuf + m);
     int *hactp = reinterpret_cast<int *>(w.hbuf + 3 * m);
@@ -727,14 +759,17 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[0], st));
         const dim3 rowgrid(std::min(cdiv(n, 256), 1024), na);
         const dim3 scalegrid(std::max(1, std::min(cdiv(n, 256 * 8), 256)), na);
-        // FP32 copy of X for the blocks that couple it to the corrections
-        k_convert<double2, float2><<<cgrid, 256, 0, st>>>(X, cntm, Xs);
+        // X and HX as FP32 hi/lo pairs: the hi part of X is its FP32 copy (for the
+        // TPA T_b and the W orthogonalisation); the pairs feed the FP64-accurate
+        // Grams and rotations on the FP32 pipe (gemm_df.cu)
+        RS_TRY(split_df(ctx, X, cntm, Xs, Xl, st));
+        RS_TRY(split_df(ctx, HX, cntm, HXh, HXl, st));
         // R = HX - X Theta of the active bands in FP64 (into Xn, free until the
         // rotation), rounded to FP32 into W
         k_residual_rows<double2><<<rowgrid, 256, 0, st>>>(HX, X, w.theta, w.act, n, Xn);
         k_convert<double2, float2><<<std::min(cdiv((long long)na * n, 256), 4096), 256, 0, st>>>(
             Xn, (long long)na * n, W);
-        count_launch(ctx, 3);
+        count_launch(ctx, 2);
         RS_LAUNCHED(ctx, "refine residual");
         if (o.precond == RSDFT_PRECOND_TPA || o.precond == RSDFT_PRECOND_LEARNED) {
             RS_TRY(project32(ctx, Xs, proj, m, st));
@@ -797,19 +832,21 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
             // (1e-5 of max |G|) in these blocks, divided by small gaps of the
             // projected problem, slowed the refinement below 1e-8
             RS_TRY(gram_pair<float2>(ctx, Y, HY, w.GS + (size_t)m * k + m, w.GH + (size_t)m * k + m, k, false, st));
-            RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
-            RowBlocks HYX{{HX, nullptr, nullptr}, {m, 0, 0}};
-            RS_TRY(gram(ctx, YX, YX, w.GS, k, true, dV, st));
-            RS_TRY(gram(ctx, YX, HYX, w.GH, k, true, dV, st));
-            RS_TRY(gram64x32(ctx, YX, Y, w.GS + m, k, dV, st));
-            RS_TRY(gram64x32(ctx, HYX, Y, w.GH + m, k, dV, st));
+            const B32 none{{nullptr, nullptr, nullptr}, {0, 0, 0}};
+            const B32 bx{{Xs, nullptr, nullptr}, {m, 0, 0}}, bxl{{Xl, nullptr, nullptr}, {m, 0, 0}};
+            const B32 bhx{{HXh, nullptr, nullptr}, {m, 0, 0}}, bhxl{{HXl, nullptr, nullptr}, {m, 0, 0}};
+            RS_TRY(gram_df(ctx, Xs, Xl, m, bx, bxl, w.GS, k, dV, st));
+            RS_TRY(gram_df(ctx, Xs, Xl, m, bhx, bhxl, w.GH, k, dV, st));
+            RS_TRY(gram_df(ctx, Xs, Xl, m, Y, none, w.GS + m, k, dV, st));
+            RS_TRY(gram_df(ctx, HXh, HXl, m, Y, none, w.GH + m, k, dV, st));
+            k_herm_block<<<dim3(cdiv(m, 32), cdiv(m, 32)), dim3(32, 8), 0, st>>>(w.GS, w.GH, k, m);
             k_mirror_block<<<dim3(cdiv(m, 32), cdiv(nwp, 32)), dim3(32, 8), 0, st>>>(w.GS, w.GH, k, m, nwp);
-            count_launch(ctx);
+            count_launch(ctx, 2);
             RS_LAUNCHED(ctx, "k_mirror_block");
         }
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[4], st));
         int nd = 0;
-        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st));
+        RS_TRY(rayleigh_ritz(ctx, w.GH, w.GS, k, m, pivot_tol, w.lam, w.Cfull, &nd, st, dense_df(o)));
         rs.dropped += nd;
         if (stats) RS_CUDA(ctx, cudaEventRecord(pe.ev[5], st));
         // P = [W P] C[m:], HP alike (FP32); X = X C[:m] + P, HX alike (FP64)
@@ -819,10 +856,8 @@ static rsdft_status lobpcg_refine(rsdft_ctx *ctx, double2 *x, int m, const rsdft
             B32 HYWP{{HW, HPn, nullptr}, {na, np_, 0}};
             RS_TRY(rotate32(ctx, YWP, cwp, m, m, nullptr, 1, P, nullptr, st));
             RS_TRY(rotate32(ctx, HYWP, cwp, m, m, nullptr, 1, HP, nullptr, st));
-            RowBlocks YX{{X, nullptr, nullptr}, {m, 0, 0}};
-            RowBlocks HYX{{HX, nullptr, nullptr}, {m, 0, 0}};
-            RS_TRY(rotate(ctx, YX, w.Cfull, m, m, nullptr, 1, Xn, nullptr, st));
-            RS_TRY(rotate(ctx, HYX, w.Cfull, m, m, nullptr, 1, HXn, nullptr, st));
+            RS_TRY(rotate_df(ctx, Xs, Xl, m, w.Cfull, m, m, Xn, st));
+            RS_TRY(rotate_df(ctx, HXh, HXl, m, w.Cfull, m, m, HXn, st));
             k_add_f32<<<cgrid, 256, 0, st>>>(Xn, P, cntm);
             k_add_f32<<<cgrid, 256, 0, st>>>(HXn, HP, cntm);
             count_launch(ctx, 2);
@@ -884,9 +919,9 @@ rsdft_status lobpcg_run(rsdft_ctx *ctx, double2 *x, int m, const rsdft_lobpcg_op
                 // reaches (their errors, ~eps32 |H|, enter the Ritz vectors scaled by
                 // the residual over the squared gap of the projected problem): it
                 // runs to REFINE32_FLOOR, the FP64 iteration finishes below
-                r = lobpcg_refine(ctx, x, m, o, std::max(o.tol, REFINE32_FLOOR), left, rs.haveP, r2, hres, stats,
-                                  &stalled, st);
-                if (r == RSDFT_OK && !r2.converged && !stalled && r2.iterations < left) stalled = true;
+                r = lobpcg_refine(ctx, x, m, o, std::max(o.tol, REFINE32_FLOOR), std::min(left, REFINE32_MAXIT),
+                                  rs.haveP, r2, hres, stats, &stalled, st);
+                if (r == RSDFT_OK && !r2.converged && !stalled && r2.iterations < left) stalled = true;   // cap or lock
                 if (r == RSDFT_OK && r2.converged && o.tol < REFINE32_FLOOR) stalled = true;
             } else {
                 r = lobpcg_t<double2>(ctx, x, x, m, o, o.tol, left, false, r2, hres, stats, st);
@@ -940,6 +975,7 @@ void rsdft_lobpcg_default_opts(rsdft_lobpcg_opts *o) {
     o->tensor_cores = 0;
     o->learned_iters = 0;
     o->refine = RSDFT_REFINE_FP32_CORRECTIONS;
+    o->dense = RSDFT_DENSE_AUTO;
 }
 
 rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
@@ -958,6 +994,8 @@ rsdft_status rsdft_lobpcg(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lo
         return fail(ctx, RSDFT_E_INVALID, "unknown precision");
     if (o.refine != RSDFT_REFINE_FP64 && o.refine != RSDFT_REFINE_FP32_CORRECTIONS)
         return fail(ctx, RSDFT_E_INVALID, "unknown refinement mode");
+    if (o.dense != RSDFT_DENSE_AUTO && o.dense != RSDFT_DENSE_FP64 && o.dense != RSDFT_DENSE_DF)
+        return fail(ctx, RSDFT_E_INVALID, "unknown dense mode");
     if (o.precond != RSDFT_PRECOND_TPA && o.precond != RSDFT_PRECOND_NONE && o.precond != RSDFT_PRECOND_LEARNED)
         return fail(ctx, RSDFT_E_INVALID, "unknown preconditioner");
     if (o.precond == RSDFT_PRECOND_LEARNED && !ctx->nn.ready)

@@ -756,19 +756,6 @@ struct MrState {
     int *done, *upd, *iters;
 };
 
-// out_b = in_b - x_b (dot_b dV), skipping bands that are done
-__global__ void k_mr_proj(double2 *out, const double2 *in, const double2 *__restrict__ x,
-                          const double2 *__restrict__ dot, double dV, long long n, const int *done) {
-    const int b = blockIdx.y;
-    if (done && done[b]) return;
-    const double2 c = make_double2(dot[b].x * dV, dot[b].y * dV);
-    for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
-        const size_t o = (size_t)b * n + i;
-        const double2 xv = x[o], v = in[o];
-        out[o] = make_double2(v.x - (xv.x * c.x - xv.y * c.y), v.y - (xv.x * c.y + xv.y * c.x));
-    }
-}
-
 // z_b = hq_b - e_b q_b (in place in hq)
 __global__ void k_mr_shift(double2 *hq, const double2 *__restrict__ q, const double *__restrict__ e, long long n,
                            const int *done) {
@@ -919,6 +906,16 @@ static rsdft_status bdot(rsdft_ctx *ctx, const double2 *a, const double2 *c, con
     return RSDFT_OK;
 }
 
+// out = Q in with Q = I - X X^H (all nb bands of the block; dV metric): a Gram
+// against X and a rotation.  out may alias in.
+static rsdft_status block_project(rsdft_ctx *ctx, const double2 *X, int nb, const double2 *in, double2 *out,
+                                  cudaStream_t st) {
+    RowBlocks YX{{X, nullptr, nullptr}, {nb, 0, 0}};
+    RowBlocks YI{{in, nullptr, nullptr}, {nb, 0, 0}};
+    RS_TRY(gram(ctx, YX, YI, ctx->ws.C, nb, false, ctx->dV, st));
+    return rotate(ctx, YX, ctx->ws.C, nb, nb, in, -1, out, nullptr, st);
+}
+
 static rsdft_status samples(rsdft_ctx *ctx, const double2 *X, int nb, double rtol, int maxit, float *U, float *B,
                             float *Y, int *iters_host, cudaStream_t st) {
     const long long n = ctx->n;
@@ -961,9 +958,9 @@ static rsdft_status samples(rsdft_ctx *ctx, const double2 *X, int nb, double rto
         RS_TRY(fft_xy_forward(ctx, Src::Plain, R, nullptr, nullptr, nullptr, nullptr, ctx->ws.T1, nb, st));
         RS_TRY(fft_z_mid(ctx, Mid::Tpa, ctx->ws.T1, tkin, nb, st));
         RS_TRY(fft_xy_inverse(ctx, ctx->ws.T1, nullptr, nullptr, Bs, nullptr, nb, st));
-        // MINRES on A t' = P r (into VP as scratch); the target is t = -t'
-        RS_TRY(bdot(ctx, X, R, nullptr, nb, 1.0, part, S, d1, st));
-        k_mr_proj<<<rg, BT, 0, st>>>(VP, R, X, d1, dV, n, nullptr);
+        // MINRES on A t' = Q r (into VP as scratch), Q = I - X X^H off the whole
+        // block; the target is t = -t'
+        RS_TRY(block_project(ctx, X, nb, R, VP, st));
         RS_TRY(bdot(ctx, VP, VP, nullptr, nb, 1.0, part, S, d2, st));
         k_mr_init<<<cdiv(nb, 128), 128, 0, st>>>(ms, d2, nb);
         k_mr_scale<<<rg, BT, 0, st>>>(V, VP, ms, n);   // v = rhs / beta1
@@ -974,16 +971,13 @@ static rsdft_status samples(rsdft_ctx *ctx, const double2 *X, int nb, double rto
         RS_CUDA(ctx, cudaMemsetAsync(T, 0, blk * sizeof(double2), st));
         std::vector<int> hdone(nb);
         for (int it = 0; it < maxit; ++it) {
-            // p = P (H - e) P v
-            RS_TRY(bdot(ctx, X, V, nullptr, nb, 1.0, part, S, d1, st));
-            k_mr_proj<<<rg, BT, 0, st>>>(Q, V, X, d1, dV, n, ms.done);
-            count_launch(ctx);
+            // p = Q (H - e) Q v (converged bands are computed too; the MINRES
+            // kernels below leave their state untouched)
+            RS_TRY(block_project(ctx, X, nb, V, Q, st));
             RS_TRY(apply_h64(ctx, Q, HQ, nb, st));
             k_mr_shift<<<rg, BT, 0, st>>>(HQ, Q, e, n, ms.done);
             count_launch(ctx);
-            RS_TRY(bdot(ctx, X, HQ, nullptr, nb, 1.0, part, S, d2, st));
-            k_mr_proj<<<rg, BT, 0, st>>>(P, HQ, X, d2, dV, n, ms.done);
-            count_launch(ctx);
+            RS_TRY(block_project(ctx, X, nb, HQ, P, st));
             // Lanczos step and its scalars
             RS_TRY(bdot(ctx, V, P, nullptr, nb, 1.0, part, S, d3, st));
             k_mr_lanczos<<<rg, BT, 0, st>>>(P, V, VP, d3, ms, n);
@@ -1003,11 +997,9 @@ static rsdft_status samples(rsdft_ctx *ctx, const double2 *X, int nb, double rto
                 if (all) break;
             }
         }
-        // t' <- P t'.  With t = -t' the target sign(Re<t|base>) t equals
+        // t' <- Q t'.  With t = -t' the target sign(Re<t|base>) t equals
         // sign(Re<t'|base>) t', so the planes come from t' directly.
-        RS_TRY(bdot(ctx, X, T, nullptr, nb, 1.0, part, S, d1, st));
-        k_mr_proj<<<rg, BT, 0, st>>>(Q, T, X, d1, dV, n, nullptr);
-        count_launch(ctx);
+        RS_TRY(block_project(ctx, X, nb, T, Q, st));
         RS_TRY(bdot(ctx, Q, Bs, nullptr, nb, 1.0, part, S, d2, st));
         RS_TRY(bdot(ctx, Q, Q, nullptr, nb, 1.0, part, S, d3, st));
         RS_TRY(bdot(ctx, Bs, Bs, nullptr, nb, 1.0, part, S, d4, st));

@@ -40,6 +40,8 @@ struct Fft3Plan {
     const float2 *tw32[3];
     const double *g2pos[3];  // G_a^2 at each digit-reversed position, device
     const float *g2pos32[3];
+    const double *gpos[3];   // G_a at each digit-reversed position (0 on the
+                             // Nyquist plane of an even axis), device
 };
 
 // Device views handed to kernels (T = double for the FP64 form, float for the
@@ -100,6 +102,7 @@ struct ScfWork {
     double *f = nullptr, *eig = nullptr;             // [nband]
     double *red = nullptr;                           // reduction scratch
     double2 *cbuf = nullptr;                         // [n] complex scratch (FFT)
+    double *gga = nullptr;                           // [4][n] PBE: grad rho, then the flux terms
 };
 
 // Learned preconditioner: weights, Adam state and scratch (precond_nn.cu).
@@ -146,6 +149,7 @@ struct rsdft_ctx {
     long long launches = 0;          // every kernel launched on this context
     long long coop_fallbacks = 0;    // tridiagonalisations that could not launch cooperatively
     int coop_last_error = 0;         // cudaError_t of the last such launch
+    int dense_mode = 0;              // rsdft_eigh / rsdft_rayleigh_ritz: RSDFT_DENSE_*
     bool autotune = false;           // time the tile candidates on the first call of a shape
     std::map<std::string, int> tuned;   // shape key -> chosen candidate
     std::string err;
@@ -191,7 +195,7 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ---- FFT / H psi (fft.cu) ---------------------------------------------------
-enum class Mid { Kinetic, Tpa, Hartree, Scale };
+enum class Mid { Kinetic, Tpa, Hartree, Scale, GradX, GradY, GradZ };
 enum class Src { Plain, Residual, RealField };
 // Forward xy-plane pass: src -> dst ([nb][n] complex).  Src::Residual reads
 // hx[act[b]] - theta[act[b]] x[act[b]]; Src::RealField reads a real [n] field
@@ -243,9 +247,21 @@ rsdft_status rotate(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, int ld
 // partials reduced in FP64; rotation coefficients rounded to FP32.
 rsdft_status gram32(rsdft_ctx *ctx, const RowBlocksT<float2> &A, const RowBlocksT<float2> &B,
                     double2 *g, int ldg, bool hermitian, double scale, cudaStream_t st);
-// FP64 rows A against FP32 rows B (converted exactly, products and sums in FP64).
-rsdft_status gram64x32(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocksT<float2> &B, double2 *g, int ldg,
-                       double scale, cudaStream_t st);
+// Split-K partial buffer of the Gram kernels (grown when needed) and its FP64
+// reduction into g (hermitian: tiles of edge te below the diagonal mirrored).
+rsdft_status ensure_gram_partials(rsdft_ctx *ctx, size_t elems);
+rsdft_status gram_reduce(rsdft_ctx *ctx, int nsplit, int na, int nb, bool hermitian, int te, double scale,
+                         double2 *g, int ldg, cudaStream_t st);
+// FP64-accurate products on the FP32 pipe (gemm_df.cu): FP64 rows held as
+// FP32 hi/lo pairs (split_df), error-free products, TwoSum accumulation.
+rsdft_status split_df(rsdft_ctx *ctx, const double2 *x, long long cnt, float2 *h, float2 *l, cudaStream_t st);
+// g[i][j] = scale * sum_r conj(A_i) B_j, A = (ah, al) [na][n], B = (bh, bl) row
+// blocks (bl all null: B exact in FP32).
+rsdft_status gram_df(rsdft_ctx *ctx, const float2 *ah, const float2 *al, int na, const RowBlocksT<float2> &bh,
+                     const RowBlocksT<float2> &bl, double2 *g, int ldg, double scale, cudaStream_t st);
+// out[b] = sum_{i < k} c[i][b] Y_i, Y = (yh, yl) [k][n], c [k][ldc] FP64, out [m][n] FP64.
+rsdft_status rotate_df(rsdft_ctx *ctx, const float2 *yh, const float2 *yl, int k, const double2 *c, int ldc, int m,
+                       double2 *out, cudaStream_t st);
 rsdft_status rotate32(rsdft_ctx *ctx, const RowBlocksT<float2> &Y, const double2 *c, int ldc, int m,
                       const float2 *base, int sign, float2 *out0, float2 *out1, cudaStream_t st);
 // Tensor-core (split-BF16, tcgen05) Grams of FP32 blocks (gram_tc.cu).
@@ -281,11 +297,18 @@ rsdft_status autotune_pick(rsdft_ctx *ctx, const std::string &key, int ncand, in
 // Held from a cooperative launch until the stream that launched it has
 // synchronised: cooperative grids of different contexts never overlap.
 std::mutex &coop_mutex();
+// df: the double-float cluster tridiagonalisation where it fits (tridiag_cl.cu)
 rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs, int k,
                            int nkeep, double pivot_tol, double *lam_dev, double2 *c_out,
-                           int *ndropped, cudaStream_t st);
+                           int *ndropped, cudaStream_t st, bool df = false);
 rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *lam_dev,
-                         double2 *z, int ldz, cudaStream_t st);
+                         double2 *z, int ldz, cudaStream_t st, bool df = false);
+// Householder tridiagonalisation of the Hermitian a (k x k, ld) in double-float
+// on one 16-CTA cluster; *done = false (and nothing launched) where k does not
+// fit in the cluster's shared memory or the cluster launch is refused.
+bool tridiag_cluster_fits(int k);
+rsdft_status tridiag_cluster(rsdft_ctx *ctx, const double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau,
+                             double *d, double *e, cudaStream_t st, bool *done);
 
 // ---- small vector kernels (lobpcg.cu / scf.cu) ----------------------------------
 rsdft_status colnorms(rsdft_ctx *ctx, const double2 *a, int nb, double *out, cudaStream_t st);

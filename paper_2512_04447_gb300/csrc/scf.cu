@@ -1,6 +1,6 @@
 // SCF step around LOBPCG (the density and potential updates that the paper
 // counts as "Others" in Fig. 1): density, FFT Hartree, LDA (Slater exchange +
-// Perdew-Zunger 1981 correlation), occupations (aufbau / Fermi-Dirac with mu
+// Perdew-Zunger 1981 correlation) or GGA-PBE, occupations (aufbau / Fermi-Dirac with mu
 // by bisection), energies, Anderson mixing.  All FP64, all on the device;
 // reductions are two-stage with a fixed order.
 #include <cmath>
@@ -70,6 +70,97 @@ __global__ void k_lda(const double *__restrict__ rho, long long n, double *eps, 
         eps[i] = e;
         vxc[i] = v;
     }
+}
+
+// ---- GGA: PBE (Perdew, Burke, Ernzerhof 1996; PW92 correlation of the uniform gas)
+// e(rho, sigma) = rho (eps_x + eps_c), sigma = |grad rho|^2, spin-unpolarised:
+//   eps_x = -(3/(4 pi)) k_F F_x(s), k_F = (3 pi^2 rho)^(1/3), s^2 = sigma/(4 k_F^2 rho^2),
+//   F_x = 1 + kappa - kappa/(1 + mu s^2/kappa);
+//   eps_c = eps_c^PW92(r_s) + H, t^2 = sigma/(4 k_s^2 rho^2), k_s^2 = 4 k_F/pi,
+//   H = gamma ln(1 + (beta/gamma) t^2 (1 + A t^2)/(1 + A t^2 + A^2 t^4)),
+//   A = (beta/gamma)/(exp(-eps_c^PW92/gamma) - 1).
+// de/drho and de/dsigma by forward-mode differentiation: every quantity carries
+// its two partial derivatives (Dual2), with the exact rules of each operation.
+constexpr double PBE_KAPPA = 0.804, PBE_BETA = 0.06672455060314922;
+constexpr double PW92_A0 = 0.031091, PW92_A1 = 0.21370;
+constexpr double PW92_B1 = 7.5957, PW92_B2 = 3.5876, PW92_B3 = 1.6382, PW92_B4 = 0.49294;
+
+struct Dual2 { double v, r, s; };   // value, d/drho, d/dsigma
+__device__ __forceinline__ Dual2 dconst(double c) { return Dual2{c, 0.0, 0.0}; }
+__device__ __forceinline__ Dual2 operator+(Dual2 a, Dual2 b) { return Dual2{a.v + b.v, a.r + b.r, a.s + b.s}; }
+__device__ __forceinline__ Dual2 operator-(Dual2 a, Dual2 b) { return Dual2{a.v - b.v, a.r - b.r, a.s - b.s}; }
+__device__ __forceinline__ Dual2 operator*(Dual2 a, Dual2 b) {
+    return Dual2{a.v * b.v, a.r * b.v + a.v * b.r, a.s * b.v + a.v * b.s};
+}
+__device__ __forceinline__ Dual2 operator*(double c, Dual2 a) { return Dual2{c * a.v, c * a.r, c * a.s}; }
+__device__ __forceinline__ Dual2 operator+(double c, Dual2 a) { return Dual2{c + a.v, a.r, a.s}; }
+__device__ __forceinline__ Dual2 operator/(Dual2 a, Dual2 b) {
+    const double q = a.v / b.v;
+    return Dual2{q, (a.r - q * b.r) / b.v, (a.s - q * b.s) / b.v};
+}
+__device__ __forceinline__ Dual2 dlog(Dual2 a) { return Dual2{log(a.v), a.r / a.v, a.s / a.v}; }
+__device__ __forceinline__ Dual2 dexp(Dual2 a) {
+    const double e = exp(a.v);
+    return Dual2{e, e * a.r, e * a.s};
+}
+__device__ __forceinline__ Dual2 dsqrt(Dual2 a) {
+    const double q = sqrt(a.v);
+    return Dual2{q, 0.5 * a.r / q, 0.5 * a.s / q};
+}
+__device__ __forceinline__ Dual2 dcbrt(Dual2 a) {
+    const double c = cbrt(a.v);
+    const double f = c / (3.0 * a.v);
+    return Dual2{c, f * a.r, f * a.s};
+}
+
+__device__ Dual2 pbe_e(Dual2 rho, Dual2 sigma) {
+    const double gamma = (1.0 - M_LN2) / (M_PI * M_PI);
+    const double mu = PBE_BETA * M_PI * M_PI / 3.0;
+    const Dual2 kf = dcbrt((3.0 * M_PI * M_PI) * rho);
+    const Dual2 ex_unif = (-0.75 / M_PI) * kf;
+    const Dual2 rho2 = rho * rho;
+    const Dual2 s2 = sigma / (4.0 * (kf * kf * rho2));
+    const Dual2 fx = dconst(1.0 + PBE_KAPPA) - PBE_KAPPA * (dconst(1.0) / (1.0 + (mu / PBE_KAPPA) * s2));
+    const Dual2 rs = dcbrt(dconst(3.0 / (4.0 * M_PI)) / rho);
+    const Dual2 srs = dsqrt(rs);
+    const Dual2 den = (2.0 * PW92_A0) * (PW92_B1 * srs + PW92_B2 * rs + PW92_B3 * (rs * srs) + PW92_B4 * (rs * rs));
+    const Dual2 ec = (-2.0 * PW92_A0) * ((1.0 + PW92_A1 * rs) * dlog(1.0 + dconst(1.0) / den));
+    const Dual2 t2 = sigma / ((16.0 / M_PI) * (kf * rho2));
+    const Dual2 A = dconst(PBE_BETA / gamma) / (dexp((-1.0 / gamma) * ec) - dconst(1.0));
+    const Dual2 at2 = A * t2;
+    const Dual2 H = gamma * dlog(1.0 + (PBE_BETA / gamma) * ((t2 * (1.0 + at2)) / (1.0 + at2 + at2 * at2)));
+    return rho * (ex_unif * fx + ec + H);
+}
+
+// Per point: eps = e/rho, vloc = de/drho, and the flux h_a = 2 de/dsigma d_a rho
+// in place of the gradient (zero where rho < 1e-12).
+__global__ void k_pbe(const double *__restrict__ rho, double *__restrict__ g0, double *__restrict__ g1,
+                      double *__restrict__ g2, long long n, double *__restrict__ eps, double *__restrict__ vloc) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[i];
+        if (!(r >= RHO_MIN)) {
+            eps[i] = 0.0;
+            vloc[i] = 0.0;
+            g0[i] = g1[i] = g2[i] = 0.0;
+            continue;
+        }
+        const double a = g0[i], b = g1[i], c = g2[i];
+        const double sg = a * a + b * b + c * c;
+        const Dual2 e = pbe_e(Dual2{r, 1.0, 0.0}, Dual2{sg, 0.0, 1.0});
+        eps[i] = e.v / r;
+        vloc[i] = e.r;
+        const double f = 2.0 * e.s;
+        g0[i] = f * a;
+        g1[i] = f * b;
+        g2[i] = f * c;
+    }
+}
+
+__global__ void k_sub_acc(double *v, const double *__restrict__ d, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        v[i] -= d[i];
 }
 
 __global__ void k_add3(const double *a, const double *b, const double *c, long long n, double *out) {
@@ -322,6 +413,36 @@ rsdft_status hartree(rsdft_ctx *ctx, const double *rho, double *vh, cudaStream_t
     return RSDFT_OK;
 }
 
+// d_a f of a real field by FFT (i G_a; the Nyquist plane of an even axis is 0)
+static rsdft_status real_derivative(rsdft_ctx *ctx, const double *f, int axis, double *out, cudaStream_t st) {
+    const Mid mid = axis == 0 ? Mid::GradX : (axis == 1 ? Mid::GradY : Mid::GradZ);
+    RS_TRY(fft_xy_forward(ctx, Src::RealField, nullptr, nullptr, nullptr, nullptr, f, ctx->scf.cbuf, 1, st));
+    RS_TRY(fft_z_mid(ctx, mid, ctx->scf.cbuf, nullptr, 1, st));
+    RS_TRY(fft_xy_inverse(ctx, ctx->scf.cbuf, nullptr, nullptr, nullptr, out, 1, st));
+    return RSDFT_OK;
+}
+
+// PBE: eps_xc and v_xc = de/drho - sum_a d_a (2 de/dsigma d_a rho)
+rsdft_status pbe(rsdft_ctx *ctx, const double *rho, double *eps, double *vxc, cudaStream_t st) {
+    RS_TRY(ensure_scf(ctx, 1, 0));
+    ScfWork &s = ctx->scf;
+    const long long n = ctx->n;
+    if (!s.gga) RS_TRY(dev_alloc(ctx, (void **)&s.gga, 4 * (size_t)n * sizeof(double)));
+    double *g[3] = {s.gga, s.gga + n, s.gga + 2 * n};
+    double *d = s.gga + 3 * n;
+    for (int a = 0; a < 3; ++a) RS_TRY(real_derivative(ctx, rho, a, g[a], st));
+    k_pbe<<<grid_for(n), 256, 0, st>>>(rho, g[0], g[1], g[2], n, eps, vxc);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_pbe");
+    for (int a = 0; a < 3; ++a) {
+        RS_TRY(real_derivative(ctx, g[a], a, d, st));
+        k_sub_acc<<<grid_for(n), 256, 0, st>>>(vxc, d, n);
+        count_launch(ctx);
+        RS_LAUNCHED(ctx, "k_sub_acc");
+    }
+    return RSDFT_OK;
+}
+
 rsdft_status lda(rsdft_ctx *ctx, const double *rho, double *eps, double *vxc, cudaStream_t st) {
     k_lda<<<grid_for(ctx->n), 256, 0, st>>>(rho, ctx->n, eps, vxc);
     count_launch(ctx);
@@ -348,12 +469,13 @@ void rsdft_scf_default_opts(rsdft_scf_opts *o) {
     o->precision = RSDFT_FP64;
     o->tensor_cores = 0;
     o->later_tol = 0.0;
+    o->xc = RSDFT_XC_LDA;
 }
 
 static rsdft_status check_scf_opts(rsdft_ctx *ctx, const rsdft_scf_opts *o, int nband) {
     if (!o || !(o->n_electrons > 0.0) || o->n_electrons > 2.0 * nband || !(o->kT >= 0.0) ||
         o->depth < 0 || o->depth > 7 || o->k_lobpcg < 0 || o->first_maxit < 0 || !(o->tol >= 0.0) ||
-        !(o->later_tol >= 0.0) ||
+        !(o->later_tol >= 0.0) || (o->xc != RSDFT_XC_LDA && o->xc != RSDFT_XC_PBE) ||
         (o->precision != RSDFT_FP64 && o->precision != RSDFT_MIXED))
         return fail(ctx, RSDFT_E_INVALID, "bad SCF options");
     return RSDFT_OK;
@@ -393,7 +515,8 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     const double dV = ctx->dV;
     // 1. effective potential from rho_in
     RS_TRY(hartree(ctx, s.rho_in, s.vh, st));
-    RS_TRY(lda(ctx, s.rho_in, s.eps, s.vxc, st));
+    if (opts->xc == RSDFT_XC_PBE) RS_TRY(pbe(ctx, s.rho_in, s.eps, s.vxc, st));
+    else RS_TRY(lda(ctx, s.rho_in, s.eps, s.vxc, st));
     k_add3<<<grid_for(n), 256, 0, st>>>(ctx->vloc, s.vh, s.vxc, n, s.veff);
     count_launch(ctx);
     RS_LAUNCHED(ctx, "k_add3");
@@ -505,6 +628,12 @@ rsdft_status rsdft_lda(rsdft_ctx *ctx, const double *rho_dev, double *eps_dev, d
     if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
     if (!rho_dev || !eps_dev || !vxc_dev) return fail(ctx, RSDFT_E_INVALID, "bad lda arguments");
     return lda(ctx, rho_dev, eps_dev, vxc_dev, as_stream(stream));
+}
+
+rsdft_status rsdft_xc_pbe(rsdft_ctx *ctx, const double *rho_dev, double *eps_dev, double *vxc_dev, void *stream) {
+    if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
+    if (!rho_dev || !eps_dev || !vxc_dev) return fail(ctx, RSDFT_E_INVALID, "bad pbe arguments");
+    return pbe(ctx, rho_dev, eps_dev, vxc_dev, as_stream(stream));
 }
 
 rsdft_status rsdft_occupations(rsdft_ctx *ctx, const double *eig_dev, int nband, double n_electrons,

@@ -24,6 +24,8 @@ OK, E_INVALID, E_GRID_NOT_5SMOOTH, E_OOM, E_CUDA, E_NOT_SPD, E_NUMERIC, E_TIMEOU
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_TPA, PRECOND_LEARNED = 0, 1, 2
 REFINE_FP64, REFINE_FP32_CORRECTIONS = 0, 1
+DENSE_AUTO, DENSE_FP64, DENSE_DF = 0, 1, 2
+XC_LDA, XC_PBE = 0, 1
 NN_HIDDEN = 8
 NN_WEIGHTS = 27 * (2 * NN_HIDDEN + 2 * NN_HIDDEN * NN_HIDDEN + NN_HIDDEN)
 STATUS_NAMES = ["OK", "E_INVALID", "E_GRID_NOT_5SMOOTH", "E_OOM", "E_CUDA", "E_NOT_SPD",
@@ -53,7 +55,7 @@ class LobpcgOpts(C.Structure):
     _fields_ = [("maxit", C.c_int), ("tol", C.c_double), ("nconv", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("lock_tol", C.c_double), ("pivot_tol", C.c_double),
                 ("switch_tol", C.c_double), ("tensor_cores", C.c_int), ("learned_iters", C.c_int),
-                ("refine", C.c_int)]
+                ("refine", C.c_int), ("dense", C.c_int)]
 
 
 class LobpcgStats(C.Structure):
@@ -70,7 +72,7 @@ class ScfOpts(C.Structure):
     _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("beta", C.c_double),
                 ("depth", C.c_int), ("k_lobpcg", C.c_int), ("first_maxit", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("precision", C.c_int),
-                ("tensor_cores", C.c_int), ("later_tol", C.c_double)]
+                ("tensor_cores", C.c_int), ("later_tol", C.c_double), ("xc", C.c_int)]
 
 
 class ScfOut(C.Structure):
@@ -105,6 +107,7 @@ _PROTOS = {
     "rsdft_rotate": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_rayleigh_ritz": (ip, [vp, vp, vp, ip, ip, dp, vp, vp, vp, vp]),
     "rsdft_eigh": (ip, [vp, vp, ip, ip, vp, vp, vp]),
+    "rsdft_set_dense": (ip, [vp, ip]),
     "rsdft_lobpcg_default_opts": (None, [C.POINTER(LobpcgOpts)]),
     "rsdft_lobpcg": (ip, [vp, vp, ip, C.POINTER(LobpcgOpts), vp, vp, C.POINTER(LobpcgStats), vp]),
     "rsdft_set_autotune": (ip, [vp, ip]),
@@ -116,8 +119,10 @@ _PROTOS = {
     "rsdft_density": (ip, [vp, vp, vp, ip, vp, vp]),
     "rsdft_hartree": (ip, [vp, vp, vp, vp]),
     "rsdft_lda": (ip, [vp, vp, vp, vp, vp]),
+    "rsdft_xc_pbe": (ip, [vp, vp, vp, vp, vp]),
     "rsdft_occupations": (ip, [vp, vp, ip, dp, dp, vp, vp, vp, vp]),
     "rsdft_scf_density": (vp, [vp]),
+    "rsdft_propagate": (ip, [vp, vp, ip, dp, ip, ip, vp]),
     "rsdft_profile_enable": (ip, [vp, ip]),
     "rsdft_profile_read": (ip, [vp, ip, vp, vp, vp, vp]),
     "rsdft_launch_count": (C.c_longlong, [vp]),
@@ -349,6 +354,9 @@ class Context:
     def set_autotune(self, on: bool = True):
         self._check(lib().rsdft_set_autotune(self._h, 1 if on else 0))
 
+    def set_dense(self, mode: int):
+        self._check(lib().rsdft_set_dense(self._h, int(mode)))
+
     def gram_bf16x3(self, a, b, g):
         self._check(lib().rsdft_gram_bf16x3(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0],
                                             _ptr(g), _stream()))
@@ -379,6 +387,11 @@ class Context:
         self._check(lib().rsdft_eigh(self._h, _ptr(a), a.shape[0], nkeep, _ptr(lam), _ptr(z_out),
                                      _stream()))
         return lam
+
+    def propagate(self, psi, dt, nsteps, order=4):
+        """rsdft_propagate: psi <- (sum_j (-i dt H)^j / j!)^nsteps psi, in place."""
+        self._check(lib().rsdft_propagate(self._h, _ptr(psi), psi.shape[0], float(dt), int(nsteps), int(order),
+                                          _stream()))
 
     # ---- LOBPCG
     @staticmethod
@@ -428,6 +441,9 @@ class Context:
 
     def lda(self, rho, eps, vxc):
         self._check(lib().rsdft_lda(self._h, _ptr(rho), _ptr(eps), _ptr(vxc), _stream()))
+
+    def xc_pbe(self, rho, eps, vxc):
+        self._check(lib().rsdft_xc_pbe(self._h, _ptr(rho), _ptr(eps), _ptr(vxc), _stream()))
 
     def occupations(self, eig, n_electrons, kT, f):
         mu, S = C.c_double(0), C.c_double(0)

@@ -40,6 +40,14 @@ def rel_err(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+# Bands of diamond8_24 whose span the subspace checks compare: the first 8 end at a
+# gap of 0.256 Ha to the 9th, while the occupied 16 end at 9.3e-4 Ha.  By the
+# Davis-Kahan sin-theta bound, sin(theta) <= ||R||_2 / gap <= sqrt(p) r_max / gap,
+# a residual tolerance of 1e-9 pins the 8-band span to 1.1e-8 per side, but the
+# 16-band span only to 4e-6.
+PREFIX8 = 8
+
+
 def subspace_distance(Xa, Xb, dV):
     """sin of the largest principal angle between span(Xa) and span(Xb)."""
     s = np.linalg.svd((Xa.conj() @ Xb.T) * dV, compute_uv=False)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle.lobpcg import lobpcg as oracle_lobpcg
-from tests.gpu_common import R, dev, host, need_gpu, pair, subspace_distance
+from tests.gpu_common import PREFIX8, R, dev, host, need_gpu, pair, subspace_distance
 from workloads import diamond8_24
 
 pytestmark = pytest.mark.gpu
@@ -34,5 +34,5 @@ def test_autotuned_lobpcg_meets_fp64_bars_and_repeats(form):
     o = oracle_lobpcg(ham, x0, maxit=200, tol=1e-9)
     assert st1.converged and st2.converged
     assert np.max(np.abs(eig2 - o.eig)) < 1e-9
-    assert subspace_distance(host(x2)[:16], o.X[:16], ham.dV) < 1e-7
+    assert subspace_distance(host(x2)[:PREFIX8], o.X[:PREFIX8], ham.dV) < 1e-7
     assert np.array_equal(eig1, eig2) or np.max(np.abs(eig1 - eig2)) < 1e-12

@@ -8,7 +8,7 @@ import pytest
 
 from oracle.lobpcg import lobpcg as oracle_lobpcg
 from oracle.scf import scf_init, scf_step
-from tests.gpu_common import R, dev, host, need_gpu, pair, rel_err, subspace_distance, torch
+from tests.gpu_common import PREFIX8, R, dev, host, need_gpu, pair, rel_err, subspace_distance, torch
 from workloads import diamond8_24, draw_x0, small_cell
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_mixed_lobpcg_meets_fp64_bars_after_refinement():
     assert stats.iterations > stats.iterations_mixed
     assert np.max(res) <= 1e-9
     assert np.max(np.abs(eig - o.eig)) < 1e-9
-    assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
+    assert subspace_distance(host(x)[:PREFIX8], o.X[:PREFIX8], ham.dV) < 1e-7
 
 
 def test_mixed_iterations_alone_reach_fp32_level():

@@ -129,3 +129,63 @@ def test_eigh_with_degenerate_clusters(k, nkeep):
     assert np.max(np.abs(lam - ref)) < 1e-12 * nrm
     assert np.allclose(Z.conj().T @ Z, np.eye(nkeep), atol=1e-12)
     assert np.max(np.abs(a @ Z - Z * lam)) < 1e-11 * nrm
+
+
+def _hermitian_with_multiplets(k, seed):
+    """Hermitian k x k with exact 2-, 3- and 6-fold eigenvalues where they fit."""
+    rng = np.random.default_rng(seed)
+    w = np.sort(rng.uniform(-3, 5, k))
+    for lo, hi in ((10, 12), (20, 23), (30, 36)):
+        if hi <= k:
+            w[lo:hi] = w[lo]
+    w = np.sort(w)
+    q, _ = np.linalg.qr(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))
+    a = (q * w) @ q.conj().T
+    return 0.5 * (a + a.conj().T), float(np.max(np.abs(w)))
+
+
+# Double-float keeps ~48 bits (unit 2^-48 = 3.6e-15); the Householder reduction's
+# backward error is a few units per step over k <= 448 steps, ~1e-11 |A| at worst,
+# and the reflectors rounded to FP64 are unitary to the same order.
+DF_BAR = 2e-11
+
+
+@pytest.mark.parametrize("k,nkeep", [(2, 1), (17, 5), (50, 50), (200, 70), (432, 144), (448, 150), (600, 200)])
+def test_eigh_double_float_cluster(k, nkeep):
+    """RSDFT_DENSE_DF: the tridiagonalisation on one 16-CTA cluster in double-float
+    (k <= 448; k = 600 takes the FP64 kernel) against LAPACK's eigenvalues."""
+    ctx = _ctx()
+    ctx.set_dense(R.DENSE_DF)
+    a, nrm = _hermitian_with_multiplets(k, 1000 + k)
+    z = torch.empty((k, nkeep), dtype=torch.complex128, device="cuda")
+    lam = ctx.eigh(dev(a), nkeep, z)
+    Z = host(z)
+    ref = np.linalg.eigvalsh(a)[:nkeep]
+    e_lam = np.max(np.abs(lam - ref)) / nrm
+    e_orth = np.max(np.abs(Z.conj().T @ Z - np.eye(nkeep)))
+    e_res = np.max(np.abs(a @ Z - Z * lam)) / nrm
+    print(f"k {k}: eigenvalues {e_lam:.1e}, orthonormality {e_orth:.1e}, residual {e_res:.1e} (of |A|)")
+    assert e_lam < DF_BAR and e_orth < DF_BAR and e_res < DF_BAR
+
+
+def test_rayleigh_ritz_double_float_cluster_matches_oracle():
+    ctx = _ctx()
+    ctx.set_dense(R.DENSE_DF)
+    k, nkeep = 432, 144
+    gh, gs = _pair(k, k)
+    c = torch.empty((k, nkeep), dtype=torch.complex128, device="cuda")
+    lam, nd = ctx.rayleigh_ritz(dev(gh), dev(gs), nkeep, c, pivot_tol=1e-8)
+    lam_o, _, nd_o = oracle_rr(gh, gs, nkeep, pivot_tol=1e-8)
+    scale = max(1.0, np.max(np.abs(lam_o)))
+    assert nd == nd_o == 0
+    assert np.max(np.abs(lam - lam_o)) < DF_BAR * scale
+    C = host(c)
+    assert np.allclose(C.conj().T @ gs @ C, np.eye(nkeep), atol=DF_BAR)
+    assert np.allclose(C.conj().T @ gh @ C, np.diag(lam), atol=DF_BAR * scale)
+
+
+def test_set_dense_rejects_unknown_mode():
+    ctx = _ctx()
+    with pytest.raises(R.RsdftError) as e:
+        ctx.set_dense(7)
+    assert e.value.status == R.E_INVALID

@@ -77,7 +77,7 @@ def test_mixed_lobpcg_with_tensor_core_grams_meets_fp64_bars():
     """Mixed form with the Gram matrices on the tensor cores: after the FP64
     refinement the eigenvalues meet the FP64 bar against the oracle."""
     from oracle.lobpcg import lobpcg as oracle_lobpcg
-    from tests.gpu_common import pair, subspace_distance
+    from tests.gpu_common import PREFIX8, pair, subspace_distance
     from workloads import diamond8_24
     wl = diamond8_24()
     ctx, ham, _ = pair(wl)
@@ -90,7 +90,7 @@ def test_mixed_lobpcg_with_tensor_core_grams_meets_fp64_bars():
           f"{stats.iterations - stats.iterations_mixed} FP64 iterations")
     assert stats.converged and stats.iterations_mixed > 0
     assert np.max(np.abs(eig - o.eig)) < 1e-9
-    assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
+    assert subspace_distance(host(x)[:PREFIX8], o.X[:PREFIX8], ham.dV) < 1e-7
 
 
 def _rot_ref(y, c, m):
@@ -145,7 +145,7 @@ def test_mixed_lobpcg_with_tensor_core_rotations_meets_fp64_bars():
     """tensor_cores = 2: Grams and Ritz rotations of the FP32 phase on tcgen05;
     after the FP64 refinement the FP64 bars hold."""
     from oracle.lobpcg import lobpcg as oracle_lobpcg
-    from tests.gpu_common import pair, subspace_distance
+    from tests.gpu_common import PREFIX8, pair, subspace_distance
     from workloads import diamond8_24
     wl = diamond8_24()
     ctx, ham, _ = pair(wl)
@@ -158,4 +158,4 @@ def test_mixed_lobpcg_with_tensor_core_rotations_meets_fp64_bars():
           f"{stats.iterations - stats.iterations_mixed} FP64 iterations")
     assert stats.converged and stats.iterations_mixed > 0
     assert np.max(np.abs(eig - o.eig)) < 1e-9
-    assert subspace_distance(host(x)[:16], o.X[:16], ham.dV) < 1e-7
+    assert subspace_distance(host(x)[:PREFIX8], o.X[:PREFIX8], ham.dV) < 1e-7
