@@ -516,6 +516,15 @@ def run_profile_case(case):
             gs = (a.conj().T @ a) / k + torch.eye(k, dtype=torch.complex128, device="cuda")
             c = torch.empty(k, k // 3, dtype=torch.complex128, device="cuda")
             ctx.rayleigh_ritz(h, gs, k // 3, c)
+    elif case == "hpsi32_64":
+        # FP32 H psi of the bench's block: 144 bands on the 64^3 grid (302 MB, above L2)
+        import workloads
+        wl = workloads.diamond64_64()
+        c64 = R.context_for(wl)
+        x = torch.randn(144, c64.n, dtype=torch.complex64, device="cuda", generator=g)
+        hx = torch.empty_like(x)
+        c64.apply_h(x, hx, precision=R.MIXED)
+        c64.apply_h(x, hx, precision=R.MIXED)
     elif case.startswith("hpsi"):
         x = torch.randn(16, ctx.n, dtype=cdt, device="cuda", generator=g)
         hx = torch.empty_like(x)
@@ -1036,7 +1045,7 @@ def main():
     ap.add_argument("--concurrent", type=int, default=8, help="batched: cells in flight")
     ap.add_argument("--profile-case", default=None,
                     help="run one small case for ncu (gram, gram_tc, rotate, rotate_tc, hpsi, hpsi32, nn_conv, "
-                         "tridiag, tridiag_df, dense) "
+                         "tridiag, tridiag_df, dense, hpsi32_64) "
                          "and exit")
     args = ap.parse_args()
     if args.profile_case:

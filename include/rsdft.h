@@ -215,9 +215,10 @@ rsdft_status rsdft_rayleigh_ritz(rsdft_ctx *ctx, const void *gh_dev, const void 
 rsdft_status rsdft_eigh(rsdft_ctx *ctx, const void *a_dev, int k, int nkeep, double *lam_host,
                         void *z_dev, void *stream);
 
-/* Arithmetic of the tridiagonalisation inside rsdft_eigh and
- * rsdft_rayleigh_ritz for this context: RSDFT_DENSE_FP64 (default; AUTO means
- * the same here) or RSDFT_DENSE_DF (as rsdft_lobpcg_opts.dense).
+/* Arithmetic of the subspace solve inside rsdft_eigh and rsdft_rayleigh_ritz
+ * for this context: RSDFT_DENSE_FP64 (default; AUTO means the same here) or
+ * RSDFT_DENSE_DF (as rsdft_lobpcg_opts.dense, the pivot_tol argument deciding
+ * the Cholesky and the triangular solves).
  * RSDFT_E_INVALID for another value. */
 rsdft_status rsdft_set_dense(rsdft_ctx *ctx, int mode);
 
@@ -265,13 +266,19 @@ typedef struct {
                               than 10%, or a residual ten times its best);
                               RSDFT_REFINE_FP64 runs them all in FP64.  Both stop
                               on the FP64 residual norms.                         */
-    int dense;             /* arithmetic of the Householder tridiagonalisation in
-                              the subspace eigensolve: RSDFT_DENSE_AUTO (default)
-                              = double-float in RSDFT_MIXED, FP64 in RSDFT_FP64;
-                              RSDFT_DENSE_FP64; RSDFT_DENSE_DF = double-float
-                              (FP32 pairs, ~2^-46 relative per operation) on one
-                              16-CTA thread-block cluster with the matrix in its
-                              shared memory, for subspaces up to 448 (FP64 above) */
+    int dense;             /* arithmetic of the subspace solve's sequential parts:
+                              RSDFT_DENSE_AUTO (default) = double-float in
+                              RSDFT_MIXED, FP64 in RSDFT_FP64; RSDFT_DENSE_FP64;
+                              RSDFT_DENSE_DF = double-float (FP32 pairs, ~2^-46
+                              relative per operation) for the Householder
+                              tridiagonalisation (one 16-CTA thread-block
+                              cluster with the matrix in its shared memory, for
+                              subspaces up to 448; FP64 above), the Sturm
+                              bisection and inverse iteration, and, where the
+                              Cholesky pivot floor is >= 1e-6 (the FP32 phase and
+                              the refinement), the Cholesky's diagonal blocks
+                              and the three triangular solves.  Results are
+                              returned in FP64 in every case.                     */
 } rsdft_lobpcg_opts;
 
 enum { RSDFT_REFINE_FP64 = 0, RSDFT_REFINE_FP32_CORRECTIONS = 1 };

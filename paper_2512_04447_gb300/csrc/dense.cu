@@ -11,6 +11,7 @@
 
 #include <mutex>
 
+#include "dfloat.h"
 #include "rsdft_internal.h"
 
 namespace rsdft {
@@ -188,6 +189,78 @@ __device__ void chol_factor_diag(const double2 *a, int ld, int kb, int nb, doubl
     }
 }
 
+// The same factorisation of the diagonal block in double-float (dfloat.h), for
+// pivot floors >= 1e-6 (the mixed form): the block's columns are a sequential
+// chain of a square root, a reciprocal and small updates, all on the FP32 pipe
+// (an FP64 square root or reciprocal is a chain of FP64 instructions of 64
+// cycles each on GB300).  sD holds complex double-floats (float4, the size of a
+// double2) during the factorisation and the FP64 factor at the end.
+__device__ void chol_factor_diag_df(const double2 *a, int ld, int kb, int nb, double floor_,
+                                    double2 (*sD)[NBK + 1], double *s_l, double *s_il, int *s_drop) {
+    float4(*sF)[NBK + 1] = reinterpret_cast<float4(*)[NBK + 1]>(sD);
+    __shared__ float2 s_ildf[NBK];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c <= r) {
+            const double2 x = ldcg2(a + (size_t)(kb + r) * ld + kb + c);
+            const dfl::df xr = dfl::from_double(x.x), xi = dfl::from_double(x.y);
+            v = make_float4(xr.h, xr.l, xi.h, xi.l);
+        }
+        sF[r][c] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+        if (threadIdx.x == 0) {
+            const dfl::df d{sF[c][c].x, sF[c][c].y};
+            const int dr = !(dfl::to_double(d) > floor_);
+            s_drop[c] = dr;
+            const dfl::df l = dr ? dfl::mk(1.0f) : dfl::sqrt(d);
+            const dfl::df il = dr ? dfl::mk(1.0f) : dfl::div(dfl::mk(1.0f), l);
+            s_l[c] = dfl::to_double(l);
+            s_il[c] = dfl::to_double(il);
+            s_ildf[c] = make_float2(il.h, il.l);
+            sF[c][c] = make_float4(l.h, l.l, 0.f, 0.f);
+        }
+        __syncthreads();
+        const int dr = s_drop[c];
+        const dfl::df inv{s_ildf[c].x, s_ildf[c].y};
+        for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+            const float4 x = sF[i][c];
+            if (dr) {
+                sF[i][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const dfl::df xr = dfl::mul(dfl::df{x.x, x.y}, inv), xi = dfl::mul(dfl::df{x.z, x.w}, inv);
+                sF[i][c] = make_float4(xr.h, xr.l, xi.h, xi.l);
+            }
+        }
+        __syncthreads();
+        if (!dr) {
+            const int m = nb - (c + 1);
+            for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
+                int ri = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+                while (ri * (ri + 1) / 2 > t) --ri;
+                while ((ri + 1) * (ri + 2) / 2 <= t) ++ri;
+                const int i = c + 1 + ri, c2 = c + 1 + (t - ri * (ri + 1) / 2);
+                // -= l_i conj(l_c2)
+                const float4 p = sF[i][c], q = sF[c2][c], x = sF[i][c2];
+                const dfl::df pr{p.x, p.y}, pi{p.z, p.w}, qr{q.x, q.y}, qi{q.z, q.w};
+                const dfl::df re = dfl::sub(dfl::df{x.x, x.y}, dfl::add(dfl::mul(pr, qr), dfl::mul(pi, qi)));
+                const dfl::df im = dfl::sub(dfl::df{x.z, x.w}, dfl::sub(dfl::mul(pi, qr), dfl::mul(pr, qi)));
+                sF[i][c2] = make_float4(re.h, re.l, im.h, im.l);
+            }
+        }
+        __syncthreads();
+    }
+    // to FP64 in place (each element read and written by one thread)
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        const float4 v = sF[r][c];
+        sD[r][c] = make_double2(dfl::to_double(dfl::df{v.x, v.y}), dfl::to_double(dfl::df{v.z, v.w}));
+    }
+    __syncthreads();
+}
+
 // Rows i >= kb+nb of the panel: l_i = a_i L11^-H by forward substitution, warp
 // wid of nw takes rows kb+nb+wid, kb+nb+wid+nw, ...
 __device__ void chol_panel_rows(double2 *a, int k, int ld, int kb, int nb, const double2 (*sD)[NBK + 1],
@@ -254,6 +327,7 @@ __device__ __forceinline__ void tri_index(int t, int &ti, int &tj) {
 
 // All panels in one cooperative launch; drop flags to drop[0..k), and the
 // kept-column list (keep[0..kc), keep[k] = kc) at the end.
+template <bool DF>
 __global__ void __launch_bounds__(256)
 k_chol_coop(double2 *a, int k, int ld, const double *floorp, int *drop, int *keep, GridSync *gs, long long limit) {
     __shared__ double2 sD[NBK][NBK + 1];
@@ -267,7 +341,8 @@ k_chol_coop(double2 *a, int k, int ld, const double *floorp, int *drop, int *kee
     const int wid = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     for (int kb = 0; kb < k; kb += NBK) {
         const int nb = min(NBK, k - kb);
-        chol_factor_diag(a, ld, kb, nb, floor_, sD, s_l, s_il, s_drop);
+        if (DF) chol_factor_diag_df(a, ld, kb, nb, floor_, sD, s_l, s_il, s_drop);
+        else chol_factor_diag(a, ld, kb, nb, floor_, sD, s_l, s_il, s_drop);
         if (blockIdx.x == 0)
             for (int c = threadIdx.x; c < nb; c += blockDim.x) drop[kb + c] = s_drop[c];
         chol_panel_rows(a, k, ld, kb, nb, sD, s_il, s_drop, wid, nw);
@@ -1105,15 +1180,17 @@ __global__ void k_cluster_gs(int k, int nkeep, const double *lam, const double *
 // Van Loan): T[j][j] = tau_j, T[0:j][j] = -tau_j T[0:j][0:j] (V[:, 0:j]^H v_j).
 constexpr int WY_NB = 32;
 
-// One CTA per block: S[a][j] = <v_a|v_j> (a < j, rows r > i0+j), then T column by
-// column in one warp; tw[blk][32][32] row-major.
+// S[a][j] = <v_a|v_j> (a < j, rows r > i0+j) of every block into tw[blk][a][j]:
+// grid (blocks, WY_G), the block's pairs spread over WY_G CTAs of 8 warps (the dot
+// products are FP64 chains: a warp FP64 instruction holds its GB300 sub-partition
+// for 64 cycles, so the pairs are spread over as many SMs as there are).
+constexpr int WY_G = 8;
 __global__ void __launch_bounds__(256)
-k_wy_tfactor(int k, const double2 *__restrict__ vh, int ldv, const double2 *__restrict__ tau,
-             double2 *__restrict__ tw) {
-    __shared__ double2 S[WY_NB][WY_NB + 1], T[WY_NB][WY_NB + 1];
+k_wy_gram(int k, const double2 *__restrict__ vh, int ldv, double2 *__restrict__ tw) {
     const int i0 = blockIdx.x * WY_NB, nr = min(WY_NB, (k - 1) - i0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int p = warp; p < WY_NB * WY_NB; p += nw) {
+    double2 *S = tw + (size_t)blockIdx.x * WY_NB * WY_NB;
+    for (int p = blockIdx.y * nw + warp; p < WY_NB * WY_NB; p += nw * gridDim.y) {
         const int a = p / WY_NB, j = p % WY_NB;
         if (a >= j || j >= nr) continue;   // uniform over the warp
         const double2 *va = vh + (size_t)(i0 + a) * ldv, *vj = vh + (size_t)(i0 + j) * ldv;
@@ -1127,26 +1204,34 @@ k_wy_tfactor(int k, const double2 *__restrict__ vh, int ldv, const double2 *__re
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-        if (lane == 0) S[a][j] = make_double2(sx, sy);
+        if (lane == 0) S[a * WY_NB + j] = make_double2(sx, sy);
     }
-    __syncthreads();
-    if (warp == 0) {
-        for (int j = 0; j < WY_NB; ++j) {
-            const double2 tj = j < nr ? tau[i0 + j] : make_double2(0.0, 0.0);
-            double2 t = make_double2(0.0, 0.0);
-            if (lane < j && j < nr) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int c = lane; c < j; ++c) c_fma(acc, T[lane][c], S[c][j]);
-                t = c_mul(make_double2(-tj.x, -tj.y), acc);
-            } else if (lane == j) {
-                t = tj;
-            }
-            T[lane][j] = t;
-            __syncwarp();
+}
+
+// One CTA (one warp) per block: T column by column from the S that k_wy_gram left in
+// tw, then T over it; tw[blk][32][32] row-major.
+__global__ void __launch_bounds__(32)
+k_wy_tfactor(int k, const double2 *__restrict__ tau, double2 *__restrict__ tw) {
+    __shared__ double2 S[WY_NB][WY_NB + 1], T[WY_NB][WY_NB + 1];
+    const int i0 = blockIdx.x * WY_NB, nr = min(WY_NB, (k - 1) - i0);
+    const int lane = threadIdx.x;
+    double2 *g = tw + (size_t)blockIdx.x * WY_NB * WY_NB;
+    for (int a = 0; a < WY_NB; ++a) S[a][lane] = (a < lane && lane < nr) ? g[a * WY_NB + lane] : make_double2(0.0, 0.0);
+    __syncwarp();
+    for (int j = 0; j < WY_NB; ++j) {
+        const double2 tj = j < nr ? tau[i0 + j] : make_double2(0.0, 0.0);
+        double2 t = make_double2(0.0, 0.0);
+        if (lane < j && j < nr) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = lane; c < j; ++c) c_fma(acc, T[lane][c], S[c][j]);
+            t = c_mul(make_double2(-tj.x, -tj.y), acc);
+        } else if (lane == j) {
+            t = tj;
         }
-        double2 *out = tw + (size_t)blockIdx.x * WY_NB * WY_NB;
-        for (int c = 0; c < WY_NB; ++c) out[lane * WY_NB + c] = T[lane][c];
+        T[lane][j] = t;
+        __syncwarp();
     }
+    for (int c = 0; c < WY_NB; ++c) g[lane * WY_NB + c] = T[lane][c];
 }
 
 // z_j = Q zt_j for each wanted eigenvector j (one CTA each, the vector in shared
@@ -1282,10 +1367,17 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         ProfScope ps(ctx, RSDFT_K_TRIEIG, kd * nkeep * (3.0 * 52.0 + 20.0), 0.0, st, 0);
         k_tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.dscr);
         count_launch(ctx);
-        // one CTA per eigenvalue: the Sturm counts and the substitutions are FP64
-        // chains, so the eigenvalues spread over the SMs
-        k_bisect<<<nkeep, BIS_T, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
-        count_launch(ctx);
+        // one CTA per eigenvalue: the Sturm counts and the substitutions are
+        // sequential chains, so the eigenvalues spread over the SMs.  The counts in
+        // double-float (df) or FP64; the inverse iteration stays FP64 either way
+        // (its vectors for eigenvalues g apart are orthogonal only to ~u ||T|| / g,
+        // with u the working precision)
+        if (df) {
+            RS_TRY(bisect_df(ctx, k, nkeep, lam_dev, st));
+        } else {
+            k_bisect<<<nkeep, BIS_T, 0, st>>>(w.d, k, nkeep, w.dscr, lam_dev);
+            count_launch(ctx);
+        }
         const size_t ii_smem = (size_t)6 * k * sizeof(double);
         static std::mutex ii_mutex;
         static size_t ii_smem_max = 0;
@@ -1320,8 +1412,9 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
         }
         if (bt_smem > bt_smem_max)
             return fail(ctx, RSDFT_E_INVALID, "subspace %d too large for the back-transformation", k);
-        k_wy_tfactor<<<cdiv(k - 1, WY_NB), 256, 0, st>>>(k, w.Vh, k, w.tau, w.Tw);
-        count_launch(ctx);
+        k_wy_gram<<<dim3(cdiv(k - 1, WY_NB), WY_G), 256, 0, st>>>(k, w.Vh, k, w.Tw);
+        k_wy_tfactor<<<cdiv(k - 1, WY_NB), 32, 0, st>>>(k, w.tau, w.Tw);
+        count_launch(ctx, 2);
         k_backtransform_wy<<<nkeep, 256, bt_smem, st>>>(k, w.Vh, k, w.Tw, w.zt, z, ldz);
         count_launch(ctx);
     }
@@ -1343,17 +1436,21 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
 // launch is refused.  Leaves the drop flags in w.drop and the kept columns in
 // w.keep (keep[k] = their count).  After a cooperative launch *coop is set and
 // `lock` holds the process-wide cooperative-launch mutex, which the caller
-// releases once the stream has synchronised.
+// releases once the stream has synchronised.  df: the diagonal blocks are
+// factored in double-float (pivot floors >= 1e-6 only).
 static rsdft_status cholesky(rsdft_ctx *ctx, int k, cudaStream_t st, std::unique_lock<std::mutex> &lock,
-                             bool *coop) {
+                             bool *coop, bool df) {
     Workspace &w = ctx->ws;
     *coop = false;
     static const int occ = [] {
         int dev = 0, cp = 0, o = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&cp, cudaDevAttrCooperativeLaunch, dev);
-        if (cp == 0 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_chol_coop, 256, 0) != cudaSuccess)
+        int o2 = 0;
+        if (cp == 0 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_chol_coop<false>, 256, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_chol_coop<true>, 256, 0) != cudaSuccess)
             o = 0;
+        o = std::min(o, o2);
         cudaGetLastError();
         return o;
     }();
@@ -1372,7 +1469,8 @@ static rsdft_status cholesky(rsdft_ctx *ctx, int k, cudaStream_t st, std::unique
         const double *fl = w.dscr + 4;
         int *dr = w.drop, *kp = w.keep;
         void *args[] = {&a, &kk, &ld, &fl, &dr, &kp, &gs, &limit};
-        const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_chol_coop, dim3(nb), dim3(256), args, 0, st);
+        const void *fn = df ? (const void *)k_chol_coop<true> : (const void *)k_chol_coop<false>;
+        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(256), args, 0, st);
         if (e == cudaSuccess) {
             count_launch(ctx);
             *coop = true;
@@ -1426,7 +1524,7 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     bool coop = false;
     {
         ProfScope pc(ctx, RSDFT_K_CHOL, 4.0 / 3.0 * kd * kd * kd, 0.0, st, 0);
-        RS_TRY(cholesky(ctx, k, st, coop_lock, &coop));
+        RS_TRY(cholesky(ctx, k, st, coop_lock, &coop, df && pivot_tol >= 1e-6));
     }
     int kc = 0;
     int *slot = reinterpret_cast<int *>(w.hbuf + w.hbuf_elems - 8);   // the front of hbuf holds LOBPCG residuals
@@ -1450,14 +1548,21 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     count_launch(ctx);
     RS_LAUNCHED(ctx, "compaction");
     const double kcd = (double)kc;
+    // the solves in double-float where the pivot floor keeps L well conditioned
+    // (L^-1 amplifies the solve's relative error by at most ~1 / sqrt(floor))
+    const bool trsm_in_df = df && pivot_tol >= 1e-6;
+    float4 *Ldf = reinterpret_cast<float4 *>(w.Lm);   // free after the compaction
     {
         ProfScope pt(ctx, RSDFT_K_TRSM, 8.0 * kcd * kcd * kcd, 0.0, st, 0);
+        if (trsm_in_df) RS_TRY(to_df(ctx, w.Km, kc, kc, Ldf, st));
         // first TRSM: Y = L^-1 G_H
-        RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Ym, kc, kc, st));
+        if (trsm_in_df) RS_TRY(trsm_df(ctx, false, Ldf, kc, w.Ym, kc, kc, st));
+        else RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Ym, kc, kc, st));
         // second TRSM: K = L^-1 Y^H
         k_conj_transpose<<<cdiv(kc2, T), T, 0, st>>>(w.Ym, kc, kc, w.Vh, kc);
         count_launch(ctx);
-        RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Vh, kc, kc, st));
+        if (trsm_in_df) RS_TRY(trsm_df(ctx, false, Ldf, kc, w.Vh, kc, kc, st));
+        else RS_TRY(trsm_lower(ctx, w.Km, kc, kc, w.Vh, kc, kc, st));
     }
     k_hermitise<<<cdiv(kc2, T), T, 0, st>>>(w.Vh, kc, kc, w.Ym, kc);
     count_launch(ctx);
@@ -1467,7 +1572,8 @@ rsdft_status rayleigh_ritz(rsdft_ctx *ctx, const double2 *gh, const double2 *gs,
     // C = L^-H Z
     {
         ProfScope pt(ctx, RSDFT_K_TRSM, 4.0 * kcd * kcd * nkeep, 0.0, st, 0);
-        RS_TRY(trsm_upperH(ctx, w.Km, kc, kc, w.Zc, nkeep, nkeep, st));
+        if (trsm_in_df) RS_TRY(trsm_df(ctx, true, Ldf, kc, w.Zc, nkeep, nkeep, st));
+        else RS_TRY(trsm_upperH(ctx, w.Km, kc, kc, w.Zc, nkeep, nkeep, st));
     }
     RS_CUDA(ctx, cudaMemsetAsync(c_out, 0, (size_t)k * nkeep * sizeof(double2), st));
     k_place_rows<<<cdiv((long long)kc * nkeep, T), T, 0, st>>>(w.Zc, kc, nkeep, w.keep, c_out);

@@ -63,8 +63,9 @@ __device__ __forceinline__ double block_sum2(double v, double *sh) {
 // FP64; FP32 blocks (mixed form) form each term in FP32, add runs of 32 terms in
 // FP32 and the run sums in FP64 (relative error ~1e-6 on the norm), which keeps
 // the FP64 pipe out of the inner loop.
+// (slice lengths are even, so that FP32 rows of even n split into 16-byte pairs)
 __device__ __forceinline__ void slice_of(long long n, int S, int s, long long &i0, long long &i1) {
-    const long long c = (n + S - 1) / S;
+    const long long c = ((n + S - 1) / S + 1) & ~1LL;
     i0 = (long long)s * c;
     i1 = i0 + c < n ? i0 + c : n;
 }
@@ -83,22 +84,47 @@ k_resid_part(const V *__restrict__ hx, const V *__restrict__ x, const double *__
     double s = 0.0, sv = 0.0;
     if constexpr (std::is_same<V, float2>::value) {
         const float th = (float)theta[b];
-        float a32 = 0.0f, v32s = 0.0f;
-        int cnt = 0;
-        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const float2 a = h[i], c = xx[i];
-            const float rx = a.x - th * c.x, ry = a.y - th * c.y;
-            a32 += rx * rx + ry * ry;
-            v32s += v32[i] * (c.x * c.x + c.y * c.y);
-            if (++cnt == 32) {
+        if ((n & 1) == 0) {
+            // pairs of points as 16-byte loads, 16 pairs per thread in flight, each
+            // run of 32 terms summed in FP32 and the runs in FP64
+            const float4 *h4 = reinterpret_cast<const float4 *>(h), *x4 = reinterpret_cast<const float4 *>(xx);
+            const float2 *v2 = reinterpret_cast<const float2 *>(v32);
+            const long long j0 = i0 >> 1, j1 = i1 >> 1;
+            for (long long jb = j0 + threadIdx.x; jb < j1; jb += 16LL * blockDim.x) {
+                float a32 = 0.0f, v32s = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const long long j = jb + (long long)u * blockDim.x;
+                    if (j < j1) {
+                        const float4 a = h4[j], c = x4[j];
+                        const float2 vv = v2[j];
+                        const float rx = a.x - th * c.x, ry = a.y - th * c.y;
+                        const float rz = a.z - th * c.z, rw = a.w - th * c.w;
+                        a32 += rx * rx + ry * ry + rz * rz + rw * rw;
+                        v32s += vv.x * (c.x * c.x + c.y * c.y) + vv.y * (c.z * c.z + c.w * c.w);
+                    }
+                }
                 s += a32;
                 sv += v32s;
-                a32 = v32s = 0.0f;
-                cnt = 0;
             }
+        } else {
+            float a32 = 0.0f, v32s = 0.0f;
+            int cnt = 0;
+            for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const float2 a = h[i], c = xx[i];
+                const float rx = a.x - th * c.x, ry = a.y - th * c.y;
+                a32 += rx * rx + ry * ry;
+                v32s += v32[i] * (c.x * c.x + c.y * c.y);
+                if (++cnt == 32) {
+                    s += a32;
+                    sv += v32s;
+                    a32 = v32s = 0.0f;
+                    cnt = 0;
+                }
+            }
+            s += a32;
+            sv += v32s;
         }
-        s += a32;
-        sv += v32s;
     } else {
         const double th = theta[b];
         for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
@@ -138,18 +164,35 @@ k_rownorm_part(const V *__restrict__ a, long long n, int S, double *__restrict__
     const V *r = a + (size_t)b * n;
     double s = 0.0;
     if constexpr (std::is_same<V, float2>::value) {
-        float a32 = 0.0f;
-        int cnt = 0;
-        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const float2 v = r[i];
-            a32 += v.x * v.x + v.y * v.y;
-            if (++cnt == 32) {
+        if ((n & 1) == 0) {   // as in k_resid_part
+            const float4 *r4 = reinterpret_cast<const float4 *>(r);
+            const long long j0 = i0 >> 1, j1 = i1 >> 1;
+            for (long long jb = j0 + threadIdx.x; jb < j1; jb += 16LL * blockDim.x) {
+                float a32 = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const long long j = jb + (long long)u * blockDim.x;
+                    if (j < j1) {
+                        const float4 v = r4[j];
+                        a32 += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                    }
+                }
                 s += a32;
-                a32 = 0.0f;
-                cnt = 0;
             }
+        } else {
+            float a32 = 0.0f;
+            int cnt = 0;
+            for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const float2 v = r[i];
+                a32 += v.x * v.x + v.y * v.y;
+                if (++cnt == 32) {
+                    s += a32;
+                    a32 = 0.0f;
+                    cnt = 0;
+                }
+            }
+            s += a32;
         }
-        s += a32;
     } else {
         for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double x = r[i].x, y = r[i].y;
@@ -519,7 +562,7 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
     if (stats) RS_TRY(pe.init(ctx));
     bool haveP = false;
     int it = 0, slow = 0;
-    double prev = -1.0;
+    double prev = -1.0, best = -1.0;
     rsdft_status result = RSDFT_OK;
     for (;;) {
         RS_TRY(resid_norms<V>(ctx, HX, X, m, st));
@@ -543,6 +586,14 @@ static rsdft_status lobpcg_t(rsdft_ctx *ctx, const V *x_in, V *x_out, int m,
             slow = rmax > 0.9 * prev ? slow + 1 : 0;
             if (slow >= 3) break;
         }
+        // FP64, below 1e-6: a max residual above twice its best so far restarts the
+        // iteration without P.  Near convergence P and W become nearly dependent; the Cholesky
+        // keeps columns down to the pivot floor, and the error of K = L^-1 G_H L^-H
+        // grows as 1 / floor along them.  Iterations of the mixed form's FP64 finish
+        // that went on with P grew the residual by ~4x per iteration from 4e-9 to
+        // 1e5 Ha on the 64^3 cell.
+        if (!fp32 && haveP && best > 0.0 && best < 1e-6 && rmax > 2.0 * best) haveP = false;
+        best = best > 0.0 ? std::min(best, rmax) : rmax;
         prev = rmax;
         int na = 0;
         for (int b = 0; b < m; ++b)

@@ -307,6 +307,15 @@ rsdft_status eigh_lowest(rsdft_ctx *ctx, double2 *a, int k, int nkeep, double *l
 // on one 16-CTA cluster; *done = false (and nothing launched) where k does not
 // fit in the cluster's shared memory or the cluster launch is refused.
 bool tridiag_cluster_fits(int k);
+// Lowest nkeep eigenvalues (lam_dev) of the tridiagonal ws.d, ws.e by
+// multisection on double-float Sturm counts; ws.dscr must hold k_tri_prep's norm
+// and bracket (trieig_df.cu).
+rsdft_status bisect_df(rsdft_ctx *ctx, int k, int nkeep, double *lam_dev, cudaStream_t st);
+// L (kc x kc, FP64) to double-float rows, and the column-parallel triangular
+// solves L X = B (back = false) or L^H X = B (back = true) on them (trsm_df.cu)
+rsdft_status to_df(rsdft_ctx *ctx, const double2 *L, int ldl, int kc, float4 *out, cudaStream_t st);
+rsdft_status trsm_df(rsdft_ctx *ctx, bool back, const float4 *L, int kc, double2 *b, int ldb, int ncol,
+                     cudaStream_t st);
 rsdft_status tridiag_cluster(rsdft_ctx *ctx, const double2 *a, int k, int ld, double2 *vh, int ldv, double2 *tau,
                              double *d, double *e, cudaStream_t st, bool *done);
 

@@ -13,13 +13,16 @@
 //   - the matrix lives in distributed shared memory: row r in CTA r mod 16,
 //     full rows of complex double-floats (16 B), so k <= 448 fits in 227 KB;
 //   - A is Hermitian, so column i below the diagonal is the conjugate of row i,
-//     which one CTA (the owner of row i) holds whole: it forms the reflector
-//     alone while the other CTAs apply the previous step's rank-2 update to
-//     their rows (the update of step i-1 is applied lazily at step i);
-//   - two cluster barriers per step: after the reflector and the updates (the
-//     others then read v_i from the owner's shared memory), and after the
-//     matrix-vector products (every CTA then reads all of y and the 16 partial
-//     sums of y^H v and forms w' redundantly);
+//     which one CTA (the owner of row i) holds whole: it brings row i up to date
+//     and forms the reflector's scalars (norm, beta, tau, the scale of v) alone,
+//     while the other CTAs apply the previous step's rank-2 update to their rows
+//     (the update of step i-1 is applied lazily at step i);
+//   - two cluster barriers per step: after the scalars and the updates (every
+//     CTA then reads row i from the owner's shared memory and forms v_i itself),
+//     and after the matrix-vector products (every CTA then reads all of y and
+//     the per-warp partial sums of y^H v and forms w' redundantly);
+//   - the FP64 outputs are written off the owner's path: vh row i by one warp of
+//     each CTA, d_i, e_i, tau_i by the next CTA;
 //   - double-float keeps about 48 significant bits, so the reduction's backward
 //     error is a small multiple of 2^-46 |A| instead of 2^-53 |A|.
 // Outputs as the FP64 kernel: d, e (real), tau, and v_i in vh row i (columns
@@ -116,13 +119,15 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
     const int R = (k + TC_C - 1) / TC_C;   // row slots per CTA
     extern __shared__ float4 sm[];
     float4 *A = sm;                        // [R][k]: row me + 16 lr in slot lr
-    float4 *Vb0 = A + (size_t)R * k;       // v of even steps, [k] (slot k-1: tau)
+    float4 *Vb0 = A + (size_t)R * k;       // v of even steps, [k]
     float4 *Vb1 = Vb0 + k;                 // v of odd steps
     float4 *YW = Vb1 + k;                  // [k]: y of all rows, then w'
     float4 *Yl = YW + k;                   // [R]: y of this CTA's rows
-    float4 *Sl = Yl + R;                   // [1]: this CTA's part of y^H v
     __shared__ float4 scratch[TC_W + 1];
     __shared__ float4 bc[4];               // scalars broadcast inside the CTA
+    __shared__ float4 pub[3];              // owner of the step: tau, scal, (beta, d_i)
+    __shared__ float4 loc[3];              // every CTA: its copy of the owner's pub
+    __shared__ float4 Sw[TC_W];            // per warp: its rows' part of y^H v
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const cdf zero{df{0.f, 0.f}, df{0.f, 0.f}};
@@ -176,30 +181,21 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
                     beta = x0.re;
                 } else {
                     // beta = -sign(Re alpha) |(alpha, x)|, tau = (beta - alpha) / beta,
-                    // scal = 1 / (alpha - beta)
+                    // scal = 1 / (alpha - beta) = conj(alpha - beta) / |alpha - beta|^2
                     const df nb = sqrt(nb2);
                     beta = x0.re.h >= 0.f ? neg(nb) : nb;
-                    t = cdf{div(sub(beta, x0.re), beta), div(neg(x0.im), beta)};
+                    const df rb = div(mk(1.0f), beta);
+                    t = cdf{mul(sub(beta, x0.re), rb), neg(mul(x0.im, rb))};
                     const cdf den{sub(x0.re, beta), x0.im};
-                    const df dd = cabs2(den);
-                    scal = cdf{div(den.re, dd), div(neg(den.im), dd)};
+                    const df rd = div(mk(1.0f), cabs2(den));
+                    scal = cdf{mul(den.re, rd), neg(mul(den.im, rd))};
                 }
-                bc[0] = st4(t);
-                bc[1] = st4(scal);
-                bc[2] = make_float4(beta.h, beta.l, 0.f, 0.f);
-                const double di = to_double(ld4(row[i]).re);
-                d[i] = di;
-                e[i] = to_double(beta);
-                tau[i] = make_double2(to_double(t.re), to_double(t.im));
+                // published for every CTA (which form v_i from row i themselves)
+                const df di = ld4(row[i]).re;
+                pub[0] = st4(t);
+                pub[1] = st4(scal);
+                pub[2] = make_float4(beta.h, beta.l, di.h, di.l);
             }
-            __syncthreads();
-            const cdf scal = ld4(bc[1]);
-            for (int q = tid; q < L; q += TC_T) {
-                const cdf vq = q == 0 ? one : cmul(cconj(ld4(row[i + 1 + q])), scal);
-                Vc[q] = st4(vq);
-                vh[(size_t)i * ldv + i + 1 + q] = make_double2(to_double(vq.re), to_double(vq.im));
-            }
-            if (tid == 0) Vc[k - 1] = bc[0];   // tau_i for the other CTAs
         }
         // ---- phase 2: step i-1's update of this CTA's rows > i (columns > i)
         if (i > 0 && nrow > 0) {
@@ -220,11 +216,25 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
             }
         }
         cl_barrier();
-        // ---- phase 3: v_i (and tau_i) from the owner, y = A v_i for own rows > i
-        if (me != owner) {
-            const float4 *src = cl.map_shared_rank(Vc, owner);
-            for (int q = tid; q < L; q += TC_T) Vc[q] = src[q];
-            if (tid == 0) Vc[k - 1] = src[k - 1];
+        // ---- phase 3: v_i from the owner's row i and scalars, y = A v_i for own rows > i
+        {
+            const float4 *prow = cl.map_shared_rank(A, owner) + (size_t)(i / TC_C) * k + (i + 1);
+            const float4 x = tid < L ? prow[tid] : make_float4(0.f, 0.f, 0.f, 0.f);   // L < TC_T
+            if (tid < 3) loc[tid] = cl.map_shared_rank(pub, owner)[tid];
+            __syncthreads();
+            const cdf scal = ld4(loc[1]);
+            if (tid < L) {
+                const cdf vq = tid == 0 ? one : cmul(cconj(ld4(x)), scal);
+                Vc[tid] = st4(vq);
+                // the FP64 copy for the back-transformation: one warp's range per CTA
+                if (warp == me) vh[(size_t)i * ldv + i + 1 + tid] = make_double2(to_double(vq.re), to_double(vq.im));
+            }
+            if (me == (owner + 1) % TC_C && tid == 0) {
+                const float4 bd = loc[2], tq = loc[0];
+                d[i] = to_double(df{bd.z, bd.w});
+                e[i] = to_double(df{bd.x, bd.y});
+                tau[i] = make_double2(to_double(df{tq.x, tq.y}), to_double(df{tq.z, tq.w}));
+            }
         }
         __syncthreads();
         cdf sp = zero;   // sum over own rows of conj(y_r) v_r
@@ -250,10 +260,7 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
                 sp = cadd(sp, cmulc(y, ld4(Vc[r - i - 1])));
             }
         }
-        {
-            const cdf s = block_sum_cdf(sp, scratch);
-            if (tid == 0) Sl[0] = st4(s);
-        }
+        if (lane == 0) Sw[warp] = st4(sp);   // summed over the cluster in phase 4
         cl_barrier();
         // ---- phase 4: all of y and y^H v, then w' = tau y - 1/2 |tau|^2 (y^H v) v
         for (int q = tid; q < L; q += TC_T) {
@@ -262,21 +269,29 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
             YW[q] = src[r / TC_C];
         }
         if (warp == 0) {
+            // y^H v: the TC_C x TC_W per-warp parts, TC_C * TC_W / 32 per lane
+            float4 part[TC_C * TC_W / 32];
+#pragma unroll
+            for (int u = 0; u < TC_C * TC_W / 32; ++u) {
+                const int idx = lane + 32 * u;
+                part[u] = cl.map_shared_rank(Sw, idx / TC_W)[idx % TC_W];
+            }
             cdf s = zero;
-            if (lane < TC_C) s = ld4(*cl.map_shared_rank(Sl, lane));
+#pragma unroll
+            for (int u = 0; u < TC_C * TC_W / 32; ++u) s = cadd(s, ld4(part[u]));
             for (int o = 16; o > 0; o >>= 1) {
                 s.re = add(s.re, shfl_df(s.re, o));
                 s.im = add(s.im, shfl_df(s.im, o));
             }
             if (lane == 0) {
-                const cdf t = ld4(Vc[k - 1]);
+                const cdf t = ld4(loc[0]);
                 const df h = mul_f(cabs2(t), -0.5f);
                 bc[3] = st4(cdf{mul(h, s.re), mul(h, s.im)});
             }
         }
         __syncthreads();
         {
-            const cdf t = ld4(Vc[k - 1]), al = ld4(bc[3]);
+            const cdf t = ld4(loc[0]), al = ld4(bc[3]);
             for (int q = tid; q < L; q += TC_T) YW[q] = st4(cadd(cmul(t, ld4(YW[q])), cmul(al, ld4(Vc[q]))));
         }
         __syncthreads();
@@ -290,9 +305,34 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
     cl_barrier();   // no CTA leaves while another may still read its shared memory
 }
 
+// Each reflector made unitary in FP64.  H = I - tau v v^H is unitary exactly when
+// 2 Re(tau) = |tau|^2 |v|^2; the double-float reduction leaves that true to about
+// 2^-46, and the back-transformed eigenvectors would be orthonormal only to
+// ~k 2^-46.  Re(tau) is reset to the root of nu a^2 - 2 a + nu b^2 = 0 (b = Im tau,
+// nu = |v|^2 summed in FP64) nearest its value: a change of ~2^-46 relative, within
+// the reduction's own backward error.  One warp per reflector.
+__global__ void __launch_bounds__(256)
+k_unitarize(int k, const double2 *__restrict__ vh, int ldv, double2 *__restrict__ tau) {
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= k - 1) return;
+    const double2 *v = vh + (size_t)i * ldv;
+    double s = 0.0;
+    for (int c = i + 1 + lane; c < k; c += 32) s = fma(v[c].x, v[c].x, fma(v[c].y, v[c].y, s));
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0 || !(s > 0.0)) return;
+    const double2 t = tau[i];
+    const double disc = 1.0 - s * s * t.y * t.y;
+    if (!(disc >= 0.0)) return;
+    const double r = ::sqrt(disc);
+    const double a_lo = s * t.y * t.y / (1.0 + r);   // (1 - r) / nu without cancellation
+    const double a_hi = (1.0 + r) / s;
+    tau[i].x = fabs(t.x - a_lo) <= fabs(t.x - a_hi) ? a_lo : a_hi;
+}
+
 size_t tridiag_cluster_smem(int k) {
     const size_t R = (size_t)(k + TC_C - 1) / TC_C;
-    return (R * k + 3 * (size_t)k + R + 1) * sizeof(float4);
+    return (R * k + 3 * (size_t)k + R) * sizeof(float4);
 }
 
 bool tridiag_cluster_fits(int k) { return k >= 2 && k <= TC_KMAX; }
@@ -346,6 +386,9 @@ rsdft_status tridiag_cluster(rsdft_ctx *ctx, const double2 *a, int k, int ld, do
     }
     count_launch(ctx);
     RS_LAUNCHED(ctx, "k_tridiag_cluster");
+    k_unitarize<<<cdiv(k - 1, 8), 256, 0, st>>>(k, vh, ldv, tau);
+    count_launch(ctx);
+    RS_LAUNCHED(ctx, "k_unitarize");
     *done = true;
     return RSDFT_OK;
 }
