@@ -181,11 +181,12 @@ def job_value(total_ms_max, steps, world):
 # capture; see profiles/traffic_mixed_tc_scf_step_64cubed.md.  A value is reported
 # only while the kernel's source body still hashes to the captured version.
 TRAFFIC = {
-    "gram_tc": {"bytes_per_launch": 1695.1e6, "kernel": "k_gram_pl", "hash": "917494c1d42fdbbb"},
-    "rotate_tc": {"bytes_per_launch": 1079.0e6, "kernel": "k_rot_pl", "hash": "f6c27c18a57e9f07"},
+    "gram_tc": {"bytes_per_launch": 1695.1e6, "kernel": "k_gram_pl", "src": "gram_tc.cu",
+                "hash": "917494c1d42fdbbb"},
+    "rotate_tc": {"bytes_per_launch": 1079.0e6, "kernel": "k_rot_pl", "src": "gram_tc.cu",
+                  "hash": "f6c27c18a57e9f07"},
 }
-TRAFFIC_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2512_04447_gb300", "csrc",
-                           "gram_tc.cu")
+CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2512_04447_gb300", "csrc")
 
 
 def kernel_body_hash(path, name):
@@ -202,7 +203,7 @@ def kernel_body_hash(path, name):
 
 def traffic_for(name):
     t = TRAFFIC.get(name)
-    if t is None or t["hash"] is None or kernel_body_hash(TRAFFIC_SRC, t["kernel"]) != t["hash"]:
+    if t is None or t["hash"] is None or kernel_body_hash(os.path.join(CSRC, t["src"]), t["kernel"]) != t["hash"]:
         return None
     return t["bytes_per_launch"]
 

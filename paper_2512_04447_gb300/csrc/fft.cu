@@ -225,9 +225,31 @@ static const ProjT<float> &proj_of(const rsdft_ctx *ctx, float2 *) { return ctx-
 static const double *v_of(const rsdft_ctx *ctx, double2 *) { return ctx->v; }
 static const float *v_of(const rsdft_ctx *ctx, float2 *) { return ctx->v32; }
 
+// Global -> shared copy of a plane or slab with several loads in flight per thread:
+// each batch issues its loads (src(i)) before any of its stores (dst(i, v)); the
+// plain loop would leave one load per thread in flight, and the passes stalled on
+// load latency well below the HBM rate.
+template <typename V, typename SrcF, typename DstF>
+__device__ __forceinline__ void stage_in(int tot, SrcF src, DstF dst) {
+    constexpr int U = sizeof(V) == 8 ? 8 : 2;
+    for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
+        V r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < tot) r[u] = src(i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < tot) dst(i, r[u]);
+        }
+    }
+}
+
 // ---- xy forward pass ------------------------------------------------------------
 template <typename V, Src SRC>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(V) == 8 ? 3 : 1)
 k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src2,
              const double *__restrict__ theta, const int *__restrict__ act,
              const double *__restrict__ rsrc, V *__restrict__ dst) {
@@ -241,22 +263,22 @@ k_xy_forward(FftTabs<V> tb, const V *__restrict__ src, const V *__restrict__ src
     const size_t off = (size_t)z * plane;
     const int RS = plane_rs(Nx);
     const unsigned nxm = tb.ax[0].nmag;
+    auto put = [&](int i, V v) { s_plane[pidx(i, Nx, RS, nxm)] = v; };
     if (SRC == Src::Plain) {
         const V *in = src + band * n + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[pidx(i, Nx, RS, nxm)] = in[i];
+        stage_in<V>((int)plane, [&](int i) { return in[i]; }, put);
     } else if (SRC == Src::Residual) {
         const int b = act[band];
         const T th = (T)theta[b];
         const V *hx = src + b * n + off;
         const V *x = src2 + b * n + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) {
-            V h = hx[i], v = x[i];
-            s_plane[pidx(i, Nx, RS, nxm)] = mk<V>(h.x - th * v.x, h.y - th * v.y);
-        }
+        stage_in<V>((int)plane, [&](int i) {
+            const V h = hx[i], v = x[i];
+            return mk<V>(h.x - th * v.x, h.y - th * v.y);
+        }, put);
     } else {
         const double *in = rsrc + off;
-        for (int i = threadIdx.x; i < (int)plane; i += blockDim.x)
-            s_plane[pidx(i, Nx, RS, nxm)] = mk<V>((T)in[i], (T)0);
+        stage_in<V>((int)plane, [&](int i) { return mk<V>((T)in[i], (T)0); }, put);
     }
     __syncthreads();
     fft_lines<V, false>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, RS, 1, true);
@@ -272,7 +294,7 @@ template <typename T> __device__ __forceinline__ T tpa_k(T x) {
 }
 
 template <typename V, Mid MID>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(V) == 8 ? 3 : 1)
 k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
     using T = typename Sc<V>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,10 +305,10 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
     const size_t zstride = (size_t)Nx * Ny;
     V *base = buf + band * n + (size_t)y * Nx;
     const int tot = Nx * Nz;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    stage_in<V>(tot, [&](int i) {
         const int z = qdiv(i, tb.ax[0].nmag), x = i - z * Nx;
-        s_slab[i] = base[z * zstride + x];
-    }
+        return base[z * zstride + x];
+    }, [&](int i, V v) { s_slab[i] = v; });
     __syncthreads();
     fft_lines<V, false>(s_slab, tb.ax[2], tb.tw[2], Nx, tb.ax[0].nmag, 1, Nx, true);
     const T inv_n = (T)tb.inv_n;
@@ -331,11 +353,29 @@ k_z_mid(FftTabs<V> tb, V *__restrict__ buf, const double *__restrict__ tkin) {
     }
 }
 
+// The four beta values of one projector-table entry (16- or 32-byte aligned: the
+// tables are [nent][4]) in one 16-byte load (FP32) or two (FP64), instead of four
+// scalar loads that each cost the L1 a wavefront per thread.
+__device__ __forceinline__ void beta4(const float *bt, float b[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(bt);
+    b[0] = q.x;
+    b[1] = q.y;
+    b[2] = q.z;
+    b[3] = q.w;
+}
+__device__ __forceinline__ void beta4(const double *bt, double b[4]) {
+    const double2 q0 = reinterpret_cast<const double2 *>(bt)[0], q1 = reinterpret_cast<const double2 *>(bt)[1];
+    b[0] = q0.x;
+    b[1] = q0.y;
+    b[2] = q1.x;
+    b[3] = q1.y;
+}
+
 // ---- xy inverse pass + epilogue ------------------------------------------------------
 enum class Epi { Plain, Hpsi, Real };
 
 template <typename V, Epi EPI>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(V) == 8 ? 3 : 1)
 k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi,
              const typename Sc<V>::T *__restrict__ v, ProjT<typename Sc<V>::T> pt,
              const V *__restrict__ p, V *__restrict__ out, double *__restrict__ rout, int stage_pe) {
@@ -350,7 +390,7 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
     const V *in = buf + band * n + off;
     const int RS = plane_rs(Nx);
     const unsigned nxm = tb.ax[0].nmag;
-    for (int i = threadIdx.x; i < (int)plane; i += blockDim.x) s_plane[pidx(i, Nx, RS, nxm)] = in[i];
+    stage_in<V>((int)plane, [&](int i) { return in[i]; }, [&](int i, V v) { s_plane[pidx(i, Nx, RS, nxm)] = v; });
     __syncthreads();
     fft_lines<V, true>(s_plane, tb.ax[1], tb.tw[1], Nx, tb.ax[0].nmag, 1, RS, true);
     fft_lines<V, true>(s_plane, tb.ax[0], tb.tw[0], Ny, tb.ax[1].nmag, RS, 1, true);
@@ -386,8 +426,11 @@ k_xy_inverse(FftTabs<V> tb, const V *__restrict__ buf, const V *__restrict__ psi
             const int e0 = pt.c_rowptr[g], e1 = pt.c_rowptr[g + 1];
             for (int e = e0; e < e1; ++e) {
                 const int a0 = pt.c_atom[e] * pt.nproj;
-                const T *bt = pt.c_beta + 4 * (size_t)e;
-                for (int j = 0; j < pt.nproj; ++j) {
+                T bt[4];
+                beta4(pt.c_beta + 4 * (size_t)e, bt);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j >= pt.nproj) break;
                     V q;
                     if (stage_pe) {
                         q = s_pe[a0 + j];
@@ -425,8 +468,8 @@ k_project(ProjT<typename Sc<V>::T> pt, const V *__restrict__ psi, V *__restrict_
         for (int j = 0; j < 4; ++j) acc[bb][j][0] = acc[bb][j][1] = (T)0;
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int g = pt.a_idx[e];
-        const T *bt = pt.a_beta + 4 * (size_t)e;
-        const T be[4] = {bt[0], bt[1], bt[2], bt[3]};
+        T be[4];
+        beta4(pt.a_beta + 4 * (size_t)e, be);
 #pragma unroll
         for (int bb = 0; bb < PROJ_BANDS; ++bb) {
             const int band = b0 + bb;
