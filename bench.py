@@ -176,15 +176,14 @@ def job_value(total_ms_max, steps, world):
     return total_ms_max / 1e3 / (steps * world)
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean over
-# the launches of one timed mixed_tc SCF step of this workload) from one ncu
-# capture; see profiles/traffic_mixed_tc_scf_step_64cubed.md.  A value is reported
-# only while the kernel's source body still hashes to the captured version.
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# roofline kernel from one ncu capture of one launch.  A value is reported only
+# while the kernel's source body still hashes to the captured version.
 TRAFFIC = {
-    "gram_tc": {"bytes_per_launch": 1695.1e6, "kernel": "k_gram_pl", "src": "gram_tc.cu",
-                "hash": "917494c1d42fdbbb"},
-    "rotate_tc": {"bytes_per_launch": 1079.0e6, "kernel": "k_rot_pl", "src": "gram_tc.cu",
-                  "hash": "f6c27c18a57e9f07"},
+    # one launch of the double-float cluster tridiagonalisation at k = 432 (the
+    # step's largest; the matrix is read once)
+    "tridiag": {"bytes_per_launch": 3.05e6, "kernel": "k_tridiag_cluster", "src": "tridiag_cl.cu",
+                "hash": "753850a2edd90f7f", "note": "k = 432 launch"},
 }
 CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2512_04447_gb300", "csrc")
 
@@ -415,6 +414,8 @@ def run_ours(args, rank, world, local_rank):
     dom = max(hk, key=lambda k: hk[k]["ms_total"])
     roofline = dict(hk[dom])
     roofline["traffic"] = traffic_for(dom)
+    if roofline["traffic"] is not None and TRAFFIC[dom].get("note"):
+        roofline["traffic_note"] = TRAFFIC[dom]["note"]
     r = res[head]
     line = {"metric": METRIC, "value": job_value(r["total_ms"], args.steps, world), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -543,7 +544,9 @@ def _fp64_peak_tf():
 def micro_dense(R, torch, sizes, reps):
     """The subspace solve of Eq. 1 (Cholesky, two triangular solves, the lowest
     k/3 eigenpairs, C = L^-H Z) on a random well-conditioned Hermitian pair of
-    size k, each part timed with CUDA events inside the library."""
+    size k, each part timed with CUDA events inside the library; in FP64 (pivot
+    floor 1e-8) and in the mixed form's double-float mode (pivot floor 1e-3, as
+    its FP32 phase uses)."""
     import numpy as np
     out = []
     ctx = R.Context((5.0, 5.0, 5.0), (8, 8, 8), np.zeros(512))
@@ -557,20 +560,23 @@ def micro_dense(R, torch, sizes, reps):
         h = torch.randn(k, k, dtype=torch.complex128, device="cuda", generator=g)
         gh = 0.5 * (h + h.conj().T) + torch.diag(torch.linspace(-2.0, 40.0, k, device="cuda")).to(torch.complex128)
         c = torch.empty(k, nkeep, dtype=torch.complex128, device="cuda")
-        ctx.rayleigh_ritz(gh, gs, nkeep, c)          # workspace and first-call set-up
-        ctx.profile_enable(True)
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            ctx.rayleigh_ritz(gh, gs, nkeep, c)
-        wall = (time.perf_counter() - t0) / reps
-        rec = {"k": k, "nkeep": nkeep, "wall_ms_per_solve": wall * 1e3}
-        for name in parts:
-            d = ctx.profile_read(R.KERNEL_NAMES.index(name))
-            ms = d["ms"] / reps
-            tf = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
-            rec[name] = {"ms": ms, "fp64_tflops": tf, "frac_fp64_peak": tf / peak}
-        ctx.profile_enable(False)
-        out.append(rec)
+        for mode, dense, ptol in (("fp64", R.DENSE_FP64, 1e-8), ("double-float", R.DENSE_DF, 1e-3)):
+            ctx.set_dense(dense)
+            ctx.rayleigh_ritz(gh, gs, nkeep, c, pivot_tol=ptol)    # workspace and first-call set-up
+            ctx.profile_enable(True)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ctx.rayleigh_ritz(gh, gs, nkeep, c, pivot_tol=ptol)
+            wall = (time.perf_counter() - t0) / reps
+            rec = {"k": k, "nkeep": nkeep, "mode": mode, "pivot_tol": ptol, "wall_ms_per_solve": wall * 1e3}
+            for name in parts:
+                d = ctx.profile_read(R.KERNEL_NAMES.index(name))
+                ms = d["ms"] / reps
+                tf = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
+                rec[name] = {"ms": ms, "fp64_tflops": tf, "frac_fp64_peak": tf / peak}
+            ctx.profile_enable(False)
+            out.append(rec)
+        ctx.set_dense(R.DENSE_FP64)
     ctx.close()
     return out
 
