@@ -19,8 +19,9 @@
 //     (the update of step i-1 is applied lazily at step i);
 //   - two cluster barriers per step: after the scalars and the updates (every
 //     CTA then reads row i from the owner's shared memory and forms v_i itself),
-//     and after the matrix-vector products (every CTA then reads all of y and
-//     the per-warp partial sums of y^H v and forms w' redundantly);
+//     and after the matrix-vector products, whose results y_r and per-warp
+//     partial sums of y^H v each CTA has stored into every CTA's shared memory
+//     (every CTA then forms w' redundantly from local data);
 //   - the FP64 outputs are written off the owner's path: vh row i by one warp of
 //     each CTA, d_i, e_i, tau_i by the next CTA;
 //   - double-float keeps about 48 significant bits, so the reduction's backward
@@ -121,13 +122,12 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
     float4 *A = sm;                        // [R][k]: row me + 16 lr in slot lr
     float4 *Vb0 = A + (size_t)R * k;       // v of even steps, [k]
     float4 *Vb1 = Vb0 + k;                 // v of odd steps
-    float4 *YW = Vb1 + k;                  // [k]: y of all rows, then w'
-    float4 *Yl = YW + k;                   // [R]: y of this CTA's rows
+    float4 *YW = Vb1 + k;                  // [k]: y of all rows (pushed by their owners), then w'
     __shared__ float4 scratch[TC_W + 1];
     __shared__ float4 bc[4];               // scalars broadcast inside the CTA
     __shared__ float4 pub[3];              // owner of the step: tau, scal, (beta, d_i)
     __shared__ float4 loc[3];              // every CTA: its copy of the owner's pub
-    __shared__ float4 Sw[TC_W];            // per warp: its rows' part of y^H v
+    __shared__ float4 Sall[TC_C * TC_W];   // every warp's part of y^H v (pushed)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const cdf zero{df{0.f, 0.f}, df{0.f, 0.f}};
@@ -255,27 +255,24 @@ k_tridiag_cluster(const double2 *__restrict__ a, int k, int ld, double2 *__restr
                 y.re = add(y.re, shfl_df(y.re, o));
                 y.im = add(y.im, shfl_df(y.im, o));
             }
-            if (lane == 0) {
-                Yl[lr] = st4(y);
-                sp = cadd(sp, cmulc(y, ld4(Vc[r - i - 1])));
-            }
+            // y_r into every CTA's YW (one remote store per lane; the stores need no
+            // reply, and the cluster barrier below makes them visible)
+            if (lane < TC_C) cl.map_shared_rank(YW, lane)[r - i - 1] = st4(y);
+            if (lane == 0) sp = cadd(sp, cmulc(y, ld4(Vc[r - i - 1])));
         }
-        if (lane == 0) Sw[warp] = st4(sp);   // summed over the cluster in phase 4
+        {   // this warp's part of y^H v into every CTA
+            const float4 sp4 = st4(sp);
+            const float4 b{__shfl_sync(0xffffffffu, sp4.x, 0), __shfl_sync(0xffffffffu, sp4.y, 0),
+                           __shfl_sync(0xffffffffu, sp4.z, 0), __shfl_sync(0xffffffffu, sp4.w, 0)};
+            if (lane < TC_C) cl.map_shared_rank(Sall, lane)[me * TC_W + warp] = b;
+        }
         cl_barrier();
-        // ---- phase 4: all of y and y^H v, then w' = tau y - 1/2 |tau|^2 (y^H v) v
-        for (int q = tid; q < L; q += TC_T) {
-            const int r = i + 1 + q;
-            const float4 *src = cl.map_shared_rank(Yl, r % TC_C);
-            YW[q] = src[r / TC_C];
-        }
+        // ---- phase 4: y^H v, then w' = tau y - 1/2 |tau|^2 (y^H v) v
         if (warp == 0) {
             // y^H v: the TC_C x TC_W per-warp parts, TC_C * TC_W / 32 per lane
             float4 part[TC_C * TC_W / 32];
 #pragma unroll
-            for (int u = 0; u < TC_C * TC_W / 32; ++u) {
-                const int idx = lane + 32 * u;
-                part[u] = cl.map_shared_rank(Sw, idx / TC_W)[idx % TC_W];
-            }
+            for (int u = 0; u < TC_C * TC_W / 32; ++u) part[u] = Sall[lane + 32 * u];
             cdf s = zero;
 #pragma unroll
             for (int u = 0; u < TC_C * TC_W / 32; ++u) s = cadd(s, ld4(part[u]));
@@ -332,7 +329,7 @@ k_unitarize(int k, const double2 *__restrict__ vh, int ldv, double2 *__restrict_
 
 size_t tridiag_cluster_smem(int k) {
     const size_t R = (size_t)(k + TC_C - 1) / TC_C;
-    return (R * k + 3 * (size_t)k + R) * sizeof(float4);
+    return (R * k + 3 * (size_t)k) * sizeof(float4);
 }
 
 bool tridiag_cluster_fits(int k) { return k >= 2 && k <= TC_KMAX; }
