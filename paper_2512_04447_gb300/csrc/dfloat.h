@@ -18,6 +18,7 @@
 // compiled without contraction (-ffp-contract=off).
 #pragma once
 #include <math.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define DF_FN __host__ __device__ __forceinline__
@@ -70,6 +71,27 @@ DF_FN float fsqrt(float a) {
     return sqrtf(a);
 #endif
 }
+
+// FP32 bit patterns (exponent tests and exact powers of two)
+DF_FN int fbits(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(x);
+#else
+    int b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+DF_FN float ffrombits(int b) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(b);
+#else
+    float x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+DF_FN int fexp(float x) { return ((fbits(x) >> 23) & 0xff) - 127; }   // unbiased exponent
 
 struct df {
     float h, l;

@@ -15,6 +15,7 @@
 // 2^-46 instead of 2^-53 left them 1e-10 from orthogonal on a test spectrum.
 #include "dfloat.h"
 #include "rsdft_internal.h"
+#include "sturm_df.h"
 
 namespace rsdft {
 
@@ -35,30 +36,6 @@ __global__ void k_tri_prep_df(const double *__restrict__ d, const double *__rest
             et[i] = make_float2(e2.h, e2.l);
         }
     }
-}
-
-__device__ __forceinline__ int fexp(float x) { return ((__float_as_int(x) >> 23) & 0xff) - 127; }
-
-__device__ int sturm_count_df(const float2 *__restrict__ dt, const float2 *__restrict__ et, int k, df x) {
-    df pm{1.0f, 0.0f};
-    df p = sub(df{dt[0].x, dt[0].y}, x);
-    if (p.h == 0.0f) p = df{-0x1p-50f, 0.0f};
-    int cnt = p.h < 0.0f ? 1 : 0;
-    for (int i = 1; i < k; ++i) {
-        const df t = sub(df{dt[i].x, dt[i].y}, x);
-        df pn = sub(mul(t, p), mul(df{et[i - 1].x, et[i - 1].y}, pm));
-        if (pn.h == 0.0f) pn = mul_f(neg(p), 0x1p-50f);
-        cnt += (pn.h < 0.0f) != (p.h < 0.0f) ? 1 : 0;
-        const int ex = max(fexp(pn.h), fexp(p.h));
-        if (ex > 60 || ex < -60) {
-            const float sc = __int_as_float((127 - ex) << 23);   // 2^-ex
-            pn = mul_f(pn, sc);
-            p = mul_f(p, sc);
-        }
-        pm = p;
-        p = pn;
-    }
-    return cnt;
 }
 
 // One CTA of BISD_T threads per eigenvalue j: each round the threads take Sturm
