@@ -21,6 +21,8 @@ checked against the paper by eye:
                      projected correction targets by MINRES
 * ``tddft``       -- real-time propagation by the Taylor series of exp(-i H dt)
 * ``gga``         -- PBE exchange-correlation (the paper's functional), FFT gradients
+* ``gamma``       -- the real-arithmetic Gamma-point LOBPCG (real orbitals, real
+                     transforms, real Gram matrices, real-symmetric Eq. 1)
 * ``scf``         -- density, FFT Hartree, LDA (Slater + Perdew-Zunger 1981),
                      occupations (aufbau / Fermi-Dirac), Anderson mixing, and
                      one SCF step (the "Others" component of Fig. 1)

@@ -62,7 +62,7 @@ def cholesky_dropping(gs: np.ndarray, pivot_tol: float):
     then exactly the Cholesky factor of G_S restricted to the kept columns.
     Returns (L, dropped_mask).
     """
-    a = np.array(gs, dtype=np.complex128)
+    a = np.array(gs, dtype=np.complex128 if np.iscomplexobj(gs) else np.float64)
     k_tot = a.shape[0]
     floor = pivot_tol * np.max(np.real(np.diag(a)))
     L = np.zeros_like(a)
@@ -110,6 +110,6 @@ def rayleigh_ritz(gh: np.ndarray, gs: np.ndarray, nkeep: int, pivot_tol: float =
     Lk = L[np.ix_(keep, keep)]
     k = reduce_to_standard(gh[np.ix_(keep, keep)], Lk)
     lam, z = np.linalg.eigh(k)
-    c = np.zeros((gs.shape[0], nkeep), dtype=np.complex128)
+    c = np.zeros((gs.shape[0], nkeep), dtype=Lk.dtype)
     c[keep] = sla.solve_triangular(Lk.conj().T, z[:, :nkeep], lower=False)
     return lam[:nkeep], c, int(np.count_nonzero(dropped))

@@ -26,6 +26,7 @@ _STREAM_EKB = 0
 _STREAM_X0 = 1
 _STREAM_NN = 2
 _STREAM_PROBE = 3
+_STREAM_X0_REAL = 4
 
 
 def diamond_sites(a: float, reps: int) -> np.ndarray:
@@ -61,6 +62,13 @@ def draw_x0(seed: int, nband: int, npts: int) -> np.ndarray:
     rng = np.random.default_rng([seed, _STREAM_X0])
     re_im = rng.standard_normal((nband, npts, 2))
     return re_im.view(np.complex128)[..., 0]
+
+
+def draw_x0_real(seed: int, nband: int, npts: int) -> np.ndarray:
+    """Initial real orbital block (Gamma-point real form): standard normal,
+    shape [nband][npts]."""
+    rng = np.random.default_rng([seed, _STREAM_X0_REAL])
+    return rng.standard_normal((nband, npts))
 
 
 def draw_probes(seed: int, nprobe: int, npts: int) -> np.ndarray:
@@ -119,6 +127,9 @@ class Workload:
 
     def x0(self, nband: int | None = None) -> np.ndarray:
         return draw_x0(self.seed, self.nband if nband is None else nband, self.npts)
+
+    def x0_real(self, nband: int | None = None) -> np.ndarray:
+        return draw_x0_real(self.seed, self.nband if nband is None else nband, self.npts)
 
 
 def _cubic(L: float) -> Tuple[float, float, float]:
