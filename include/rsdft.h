@@ -326,6 +326,47 @@ rsdft_status rsdft_lobpcg_batched(rsdft_ctx *const *ctxs, int ncell, void *const
                                   int *failed_cell);
 
 /* ---------------------------------------------------------------------------
+ * Real Gamma-point form (the paper's real-symmetric case: its eigensolver
+ * benchmark for real-symmetric matrices, Fig. 3a, beside the Hermitian Fig. 3b).
+ * At Gamma, with the context's real V_loc and real projectors, H is real
+ * symmetric and the orbitals are real.  Orbital blocks here are float64
+ * [nband][n] real arrays on the device (x fastest, as the complex blocks).
+ * Internally two real bands share one complex row, so each complex H psi
+ * transform carries two bands, and the Gram and rotation kernels form real
+ * products only (a quarter of the complex form's arithmetic).  The subspace
+ * problem of Eq. 1 is real symmetric; it runs through the Hermitian dense core
+ * with zero imaginary parts, which stay exactly zero.  Same ownership, stream
+ * and error rules as the complex calls; the workspace of the context is reused
+ * (these calls and the complex ones may alternate on one context).
+ * ------------------------------------------------------------------------- */
+
+/* hx = H x for nband real orbitals (x, hx: float64 [nband][n], device; they
+ * must not overlap).  nband == 0 is a no-op. */
+rsdft_status rsdft_apply_h_real(rsdft_ctx *ctx, const void *x_dev, void *hx_dev, int nband, void *stream);
+
+/* g[i][j] = sum_r a_i(r) b_j(r) dV (float64 [na][nb], device) over real rows
+ * a [na][n] and b [nb][n].  When a_dev == b_dev and na == nb, G is formed as a
+ * symmetric matrix (tiles on and above the diagonal, the rest mirrored). */
+rsdft_status rsdft_gram_real(rsdft_ctx *ctx, const void *a_dev, int na, const void *b_dev, int nb, void *g_dev,
+                             void *stream);
+
+/* out[b] = base[b] + sign * sum_{i<k} c[i][b] y_i for b < m: y float64 [k][n],
+ * c float64 [k][m], base float64 [m][n] or NULL (then 0), sign +-1, out float64
+ * [m][n] (may equal base).  All device. */
+rsdft_status rsdft_rotate_real(rsdft_ctx *ctx, const void *y_dev, int k, const void *c_dev, int m,
+                               const void *base_dev, int sign, void *out_dev, void *stream);
+
+/* LOBPCG of the real form: x_dev float64 [nband][n] (device, in/out: start
+ * block in, Ritz vectors out, <x_i|x_j> = delta_ij).  Options as rsdft_lobpcg
+ * with precision RSDFT_FP64 only and precond RSDFT_PRECOND_TPA or
+ * RSDFT_PRECOND_NONE (RSDFT_E_INVALID otherwise); nconv, tol, maxit,
+ * lock_tol, pivot_tol and dense keep their meaning.  The stats' per-phase
+ * times are not filled.  Returns RSDFT_E_NOT_CONVERGED when tol > 0 was not
+ * met within maxit (the block is still written back). */
+rsdft_status rsdft_lobpcg_real(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_lobpcg_opts *opts,
+                               double *eig_host, double *resnorm_host, rsdft_lobpcg_stats *stats, void *stream);
+
+/* ---------------------------------------------------------------------------
  * SCF step: V_eff = V_loc + V_H[rho_in] + v_xc[rho_in] (FFT Hartree, LDA
  * Slater + Perdew-Zunger 1981), LOBPCG (converged on the first step, k_lobpcg
  * iterations afterwards), occupations (aufbau, or Fermi-Dirac at kT > 0),

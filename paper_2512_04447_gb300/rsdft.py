@@ -123,6 +123,10 @@ _PROTOS = {
     "rsdft_occupations": (ip, [vp, vp, ip, dp, dp, vp, vp, vp, vp]),
     "rsdft_scf_density": (vp, [vp]),
     "rsdft_propagate": (ip, [vp, vp, ip, dp, ip, ip, vp]),
+    "rsdft_apply_h_real": (ip, [vp, vp, vp, ip, vp]),
+    "rsdft_gram_real": (ip, [vp, vp, ip, vp, ip, vp, vp]),
+    "rsdft_rotate_real": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
+    "rsdft_lobpcg_real": (ip, [vp, vp, ip, C.POINTER(LobpcgOpts), vp, vp, C.POINTER(LobpcgStats), vp]),
     "rsdft_profile_enable": (ip, [vp, ip]),
     "rsdft_profile_read": (ip, [vp, ip, vp, vp, vp, vp]),
     "rsdft_launch_count": (C.c_longlong, [vp]),
@@ -408,6 +412,26 @@ class Context:
         stats = LobpcgStats()
         st = self._check(lib().rsdft_lobpcg(self._h, _ptr(x), m, C.byref(opts), _ptr(eig), _ptr(res),
                                             C.byref(stats), _stream()), allow=(E_NOT_CONVERGED,))
+        return eig, res, stats, st
+
+    # ---- real Gamma-point form (float64 [nband][n] real blocks)
+    def apply_h_real(self, x, hx):
+        self._check(lib().rsdft_apply_h_real(self._h, _ptr(x), _ptr(hx), x.shape[0], _stream()))
+
+    def gram_real(self, a, b, g):
+        self._check(lib().rsdft_gram_real(self._h, _ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(g),
+                                          _stream()))
+
+    def rotate_real(self, y, c, out, base=None, sign=1):
+        self._check(lib().rsdft_rotate_real(self._h, _ptr(y), y.shape[0], _ptr(c), c.shape[1], _ptr(base),
+                                            sign, _ptr(out), _stream()))
+
+    def lobpcg_real(self, x, opts: LobpcgOpts):
+        m = x.shape[0]
+        eig, res = np.zeros(m), np.zeros(m)
+        stats = LobpcgStats()
+        st = self._check(lib().rsdft_lobpcg_real(self._h, _ptr(x), m, C.byref(opts), _ptr(eig), _ptr(res),
+                                                 C.byref(stats), _stream()), allow=(E_NOT_CONVERGED,))
         return eig, res, stats, st
 
     # ---- SCF
