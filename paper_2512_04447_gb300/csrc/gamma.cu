@@ -475,13 +475,14 @@ rsdft_status gram_pair(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, d
 // out0[b] = base[b] + sign sum_i Re c[i][b] y_i over the real bands y_i of the
 // pair-row blocks of Y, for m output bands (pairs_of(m) pair rows; the .y half
 // of the last row is base's, or 0, when m is odd).  Blocks are consumed in the
-// order 1, 2, 0 so that out1 (optional) = the block 1-2 part alone.  Tile: 32
-// output pair rows x 64 points; thread (ty, tx) owns pair rows ty, ty + 16 and
+// order 1, 2, 0 so that out1 (optional) = the block 1-2 part alone.  Tile: 16 PB
+// output pair rows x 64 points; thread (ty, tx) owns pair rows ty + 16 p and
 // points tx + 16 q.
+template <int PB>
 __global__ void __launch_bounds__(GR_THREADS)
 k_rotate_pair(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long long n, const double2 *base, int sign,
               double2 *out0, double2 *out1) {
-    constexpr int TB = 32;
+    constexpr int TB = 16 * PB;
     __shared__ double2 Ys[GRK][GRPTS + 1];
     __shared__ double2 Ca[GRK][TB + 1];   // (c[2i][2b'], c[2i][2b'+1])   input band 2i -> output pair b'
     __shared__ double2 Cb[GRK][TB + 1];   // (c[2i+1][2b'], c[2i+1][2b'+1])
@@ -489,9 +490,9 @@ k_rotate_pair(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long l
     const long long r0 = (long long)blockIdx.y * GRPTS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int mp = pairs_of(m);
-    double ax[2][4], ay[2][4];
+    double ax[PB][4], ay[PB][4];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < PB; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) ax[p][q] = ay[p][q] = 0.0;
 #pragma unroll 1
@@ -531,16 +532,16 @@ k_rotate_pair(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long l
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < GRK; ++k) {
-                double2 ca[2], cb[2], yv[4];
+                double2 ca[PB], cb[PB], yv[4];
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
+                for (int p = 0; p < PB; ++p) {
                     ca[p] = Ca[k][ty + 16 * p];
                     cb[p] = Cb[k][ty + 16 * p];
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) yv[q] = Ys[k][tx + 16 * q];
 #pragma unroll
-                for (int p = 0; p < 2; ++p)
+                for (int p = 0; p < PB; ++p)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         ax[p][q] = fma(yv[q].x, ca[p].x, fma(yv[q].y, cb[p].x, ax[p][q]));
@@ -551,7 +552,7 @@ k_rotate_pair(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long l
         }
         if (oi == 1 && out1) {
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < PB; ++p) {
                 const int bp = b0 + ty + 16 * p;
                 if (bp >= mp) continue;
 #pragma unroll
@@ -564,7 +565,7 @@ k_rotate_pair(RowBlocks Y, const double2 *__restrict__ c, int ldc, int m, long l
     }
     const double sg = (double)sign;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < PB; ++p) {
         const int bp = b0 + ty + 16 * p;
         if (bp >= mp) continue;
 #pragma unroll
@@ -590,8 +591,13 @@ rsdft_status rotate_pair(rsdft_ctx *ctx, const RowBlocks &Y, const double2 *c, i
     const int mp = pairs_of(m);
     ProfScope ps(ctx, RSDFT_K_ROTATE, 2.0 * (double)ctx->n * k * m,
                  (double)sizeof(double2) * (double)ctx->n * (kp + mp + (out1 ? mp : 0) + (base ? mp : 0)), st);
-    k_rotate_pair<<<dim3(cdiv(mp, 32), cdiv(ctx->n, GRPTS)), GR_THREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base, sign,
-                                                                                 out0, out1);
+    // output tile of 16 or 32 pair rows, the one with less padding (ties: 32)
+    if (cdiv(mp, 16) * 16 < cdiv(mp, 32) * 32)
+        k_rotate_pair<1><<<dim3(cdiv(mp, 16), cdiv(ctx->n, GRPTS)), GR_THREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base,
+                                                                                        sign, out0, out1);
+    else
+        k_rotate_pair<2><<<dim3(cdiv(mp, 32), cdiv(ctx->n, GRPTS)), GR_THREADS, 0, st>>>(Y, c, ldc, m, ctx->n, base,
+                                                                                        sign, out0, out1);
     RS_LAUNCHED(ctx, "k_rotate_pair");
     return RSDFT_OK;
 }

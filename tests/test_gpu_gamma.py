@@ -67,7 +67,9 @@ def test_gram_real_symmetric_tiles(na):
     assert np.array_equal(G, G.T)
 
 
-@pytest.mark.parametrize("k,m,with_base", [(1, 1, False), (5, 3, True), (45, 19, True), (130, 67, False)])
+# output tiles of 16 pair rows (m = 1, 3, 19, 67) and of 32 (m = 60, 128)
+@pytest.mark.parametrize("k,m,with_base", [(1, 1, False), (5, 3, True), (45, 19, True), (130, 67, False),
+                                           (70, 60, True), (200, 128, False)])
 def test_rotate_real_matches_oracle(k, m, with_base):
     ctx = _ctx()
     y = draw_x0_real(4, k, ctx.n)
