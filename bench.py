@@ -485,6 +485,17 @@ def run_profile_case(case):
         y = torch.randn(432, ctx.n, dtype=torch.complex64, device="cuda", generator=g)
         gm = torch.empty(432, 432, dtype=torch.complex128, device="cuda")
         ctx.gram_bf16x3(y, y, gm)
+    elif case in ("gram_real", "rotate_real"):
+        # the real Gamma-point form: a 432-band real block (382 MB) as pair rows,
+        # symmetric Gram, or rotation into 144 bands
+        y = torch.randn(432, ctx.n, dtype=torch.float64, device="cuda", generator=g)
+        if case == "gram_real":
+            gm = torch.empty(432, 432, dtype=torch.float64, device="cuda")
+            ctx.gram_real(y, y, gm)
+        else:
+            c = torch.randn(432, 144, dtype=torch.float64, device="cuda", generator=g)
+            out = torch.empty(144, ctx.n, dtype=torch.float64, device="cuda")
+            ctx.rotate_real(y, c, out)
     elif case.startswith("gram") or case.startswith("rotate"):
         y = torch.randn(432, ctx.n, dtype=torch.complex128, device="cuda", generator=g)
         if case.startswith("gram"):
@@ -1122,7 +1133,7 @@ def main():
     ap.add_argument("--concurrent", type=int, default=8, help="batched: cells in flight")
     ap.add_argument("--profile-case", default=None,
                     help="run one small case for ncu (gram, gram_tc, rotate, rotate_tc, hpsi, hpsi32, nn_conv, "
-                         "tridiag, tridiag_df, dense, hpsi32_64) "
+                         "tridiag, tridiag_df, dense, hpsi32_64, gram_real, rotate_real) "
                          "and exit")
     args = ap.parse_args()
     if args.profile_case:
