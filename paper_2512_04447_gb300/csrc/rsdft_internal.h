@@ -285,11 +285,12 @@ rsdft_status rotate_tc(rsdft_ctx *ctx, const float2 *y, int k, const double2 *c,
                        float2 *out0, float2 *out1, cudaStream_t st);
 
 // ---- autotuner (context.cu) --------------------------------------------------
-// With ctx->autotune set, the first call of a shape runs each candidate once on
-// the stream, timed with CUDA events, and remembers the fastest under `key`
-// (later calls reuse it; without autotune the closed-form choice is used).
-// run(i) launches candidate i; the winner is run last so that its result is the
-// one left in the outputs.  Only for calls whose outputs do not alias inputs.
+// With ctx->autotune set, the first call of a shape runs each candidate once
+// untimed and twice timed with CUDA events on the stream, and remembers the one
+// with the fastest timed run under `key` (later calls reuse it; without
+// autotune the closed-form choice is used).  run(i) launches candidate i; the
+// winner is run last so that its result is the one left in the outputs.  Only
+// for calls whose outputs do not alias inputs.
 rsdft_status autotune_pick(rsdft_ctx *ctx, const std::string &key, int ncand, int fallback, cudaStream_t st,
                            const std::function<rsdft_status(int)> &run, int *chosen);
 
