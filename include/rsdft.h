@@ -415,6 +415,14 @@ rsdft_status rsdft_scf_init(rsdft_ctx *ctx, int nband, const rsdft_scf_opts *opt
 rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
                             rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream);
 
+/* The same SCF step on the real orbitals of the Gamma-point form (x_dev: float64
+ * [nband][n], device, in/out): LOBPCG by rsdft_lobpcg_real, rho = sum_b f_b x_b^2.
+ * opts->precision must be RSDFT_FP64 (RSDFT_E_INVALID otherwise); tensor_cores
+ * is ignored; precond RSDFT_PRECOND_TPA or RSDFT_PRECOND_NONE.  Shares the SCF
+ * state of rsdft_scf_init with the complex step (one kind of step per run). */
+rsdft_status rsdft_scf_step_real(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
+                                 rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream);
+
 /* SCF field pieces, each on [n] doubles on the device:
  * rho = sum_b f_b |x_b|^2 (x_dev [nband][n] complex128, f_dev [nband]);
  * V_H by FFT Poisson (G = 0 term removed);

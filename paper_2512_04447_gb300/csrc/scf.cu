@@ -41,6 +41,20 @@ __global__ void k_density(const double2 *__restrict__ x, const double *__restric
     }
 }
 
+// rho = sum_b f_b x_b^2 over real orbitals [nb][n] (the real Gamma-point form)
+__global__ void k_density_real(const double *__restrict__ x, const double *__restrict__ f, int nb, long long n,
+                               double *__restrict__ rho) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double v = x[(size_t)b * n + i];
+            s += f[b] * v * v;
+        }
+        rho[i] = s;
+    }
+}
+
 __device__ __forceinline__ void lda_point(double rho, double &eps, double &v) {
     if (!(rho >= RHO_MIN)) { eps = 0.0; v = 0.0; return; }
     const double cx = -0.75 * cbrt(3.0 / M_PI);
@@ -501,11 +515,15 @@ const double *rsdft_scf_density(const rsdft_ctx *ctx) {
     return (ctx && ctx->scf.ready) ? ctx->scf.rho_in : nullptr;
 }
 
-rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
-                            rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream) {
+// One SCF step on complex orbitals (real = false) or on the real orbitals of the
+// Gamma-point form (real = true: float64 [nband][n], FP64 only).
+static rsdft_status scf_step_impl(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
+                                  rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream, bool real) {
     if (!ctx) return fail(nullptr, RSDFT_E_INVALID, "ctx is NULL");
     if (!x_dev || nband <= 0 || 3LL * nband > ctx->n) return fail(ctx, RSDFT_E_INVALID, "bad x/nband");
     RS_TRY(check_scf_opts(ctx, opts, nband));
+    if (real && opts->precision != RSDFT_FP64)
+        return fail(ctx, RSDFT_E_INVALID, "the real Gamma-point SCF step runs in FP64 only");
     ScfWork &s = ctx->scf;
     if (!s.ready) return fail(ctx, RSDFT_E_INVALID, "call rsdft_scf_init first");
     if (opts->depth + 1 > s.hist_cap || nband > s.nband)
@@ -532,7 +550,8 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     else if (opts->later_tol > 0.0) { lo.maxit = opts->first_maxit; lo.tol = opts->later_tol; }
     else { lo.maxit = opts->k_lobpcg; lo.tol = 0.0; lo.switch_tol = 0.0; }
     rsdft_lobpcg_stats ls{};
-    rsdft_status lst = lobpcg_run(ctx, (double2 *)x_dev, nband, lo, nullptr, nullptr, &ls, st);
+    rsdft_status lst = real ? rsdft_lobpcg_real(ctx, x_dev, nband, &lo, nullptr, nullptr, &ls, stream)
+                            : lobpcg_run(ctx, (double2 *)x_dev, nband, lo, nullptr, nullptr, &ls, st);
     if (lst != RSDFT_OK && lst != RSDFT_E_NOT_CONVERGED) return lst;
     double *eig = ctx->ws.theta;
     // 3. occupations
@@ -540,7 +559,13 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     count_launch(ctx);
     RS_LAUNCHED(ctx, "k_occupations");
     // 4. rho_out
-    RS_TRY(density(ctx, (const double2 *)x_dev, s.f, nband, s.rho_out, st));
+    if (real) {
+        k_density_real<<<grid_for(n), 256, 0, st>>>((const double *)x_dev, s.f, nband, n, s.rho_out);
+        count_launch(ctx);
+        RS_LAUNCHED(ctx, "k_density_real");
+    } else {
+        RS_TRY(density(ctx, (const double2 *)x_dev, s.f, nband, s.rho_out, st));
+    }
     // 5. energies
     double *part = s.red + RED_PART;
     double *sums = s.red + RED_ENERGY;
@@ -607,6 +632,16 @@ rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_
     if (!std::isfinite(e_band) || !std::isfinite(drho))
         return fail(ctx, RSDFT_E_NUMERIC, "non-finite SCF energy or density change");
     return RSDFT_OK;
+}
+
+rsdft_status rsdft_scf_step(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
+                            rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream) {
+    return scf_step_impl(ctx, x_dev, nband, opts, out, eig_host, occ_host, stream, false);
+}
+
+rsdft_status rsdft_scf_step_real(rsdft_ctx *ctx, void *x_dev, int nband, const rsdft_scf_opts *opts,
+                                 rsdft_scf_out *out, double *eig_host, double *occ_host, void *stream) {
+    return scf_step_impl(ctx, x_dev, nband, opts, out, eig_host, occ_host, stream, true);
 }
 
 rsdft_status rsdft_density(rsdft_ctx *ctx, const void *x_dev, const double *f_dev, int nband,

@@ -127,6 +127,7 @@ _PROTOS = {
     "rsdft_gram_real": (ip, [vp, vp, ip, vp, ip, vp, vp]),
     "rsdft_rotate_real": (ip, [vp, vp, ip, vp, ip, vp, ip, vp, vp]),
     "rsdft_lobpcg_real": (ip, [vp, vp, ip, C.POINTER(LobpcgOpts), vp, vp, C.POINTER(LobpcgStats), vp]),
+    "rsdft_scf_step_real": (ip, [vp, vp, ip, C.POINTER(ScfOpts), C.POINTER(ScfOut), vp, vp, vp]),
     "rsdft_profile_enable": (ip, [vp, ip]),
     "rsdft_profile_read": (ip, [vp, ip, vp, vp, vp, vp]),
     "rsdft_launch_count": (C.c_longlong, [vp]),
@@ -452,6 +453,15 @@ class Context:
         eig, occ = np.zeros(m), np.zeros(m)
         self._check(lib().rsdft_scf_step(self._h, _ptr(x), m, C.byref(opts), C.byref(out), _ptr(eig),
                                          _ptr(occ), _stream()))
+        return out, eig, occ
+
+    def scf_step_real(self, x, opts: ScfOpts):
+        """rsdft_scf_step_real: the SCF step on real Gamma-point orbitals (float64 [m][n])."""
+        m = x.shape[0]
+        out = ScfOut()
+        eig, occ = np.zeros(m), np.zeros(m)
+        self._check(lib().rsdft_scf_step_real(self._h, _ptr(x), m, C.byref(opts), C.byref(out), _ptr(eig),
+                                              _ptr(occ), _stream()))
         return out, eig, occ
 
     def scf_density_ptr(self) -> int:

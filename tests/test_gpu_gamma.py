@@ -188,3 +188,37 @@ def test_lobpcg_real_rejects_unsupported_options(kw):
     with pytest.raises(R.RsdftError) as e:
         ctx.lobpcg_real(x, ctx.lobpcg_opts(**kw))
     assert e.value.status == R.E_INVALID
+
+
+def test_scf_steps_real_match_oracle_small_cell():
+    """Eight SCF steps of the real form against the oracle's SCF steps from the
+    same real start (the oracle's complex LOBPCG keeps a real start real, and its
+    first-step eigenpairs equal the Gamma-point oracle's, test_oracle_gamma)."""
+    from oracle.scf import scf_init, scf_step
+    wl = small_cell(N=(12, 12, 12), L=(6.0, 6.0, 6.0), natom=2, nband=6)
+    ctx, ham, v_loc = pair(wl)
+    n_el = 8.0
+    x0 = wl.x0_real()
+    opts = ctx.scf_opts(n_electrons=n_el, kT=0.0, beta=0.3, depth=4, k_lobpcg=3, first_maxit=200, tol=1e-8)
+    ctx.scf_init(6, opts)
+    st = scf_init(ham.grid, n_el, x0.astype(np.complex128), beta=0.3, depth=4)
+    x = dev(x0)
+    for step in range(8):
+        out, eig, occ = ctx.scf_step_real(x, opts)
+        o = scf_step(ham, v_loc, st, n_el, 0.0, k_lobpcg=3, first_maxit=200, tol=1e-8)
+        assert abs(out.e_tot - o.e_tot) / wl.natom < 1e-8, step
+        assert np.max(np.abs(eig - o.eig)) < 1e-9, step
+        assert abs(out.drho - o.drho) < 1e-8, step
+        assert np.array_equal(occ, o.f)
+    X = host(x)
+    assert np.allclose(gram_real(X, X, ham.dV), np.eye(6), atol=1e-12)
+
+
+def test_scf_step_real_rejects_mixed_precision():
+    wl = small_cell(N=(12, 12, 12), L=(6.0, 6.0, 6.0), natom=2, nband=6)
+    ctx, ham, _ = pair(wl)
+    opts = ctx.scf_opts(n_electrons=8.0, kT=0.0, precision=R.MIXED)
+    ctx.scf_init(6, opts)
+    with pytest.raises(R.RsdftError) as e:
+        ctx.scf_step_real(dev(wl.x0_real()), opts)
+    assert e.value.status == R.E_INVALID
