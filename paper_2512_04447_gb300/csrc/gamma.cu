@@ -462,13 +462,20 @@ rsdft_status gram_pair(rsdft_ctx *ctx, const RowBlocks &A, const RowBlocks &B, d
     const int nb = B.cnt[0] + B.cnt[1] + B.cnt[2];
     if (na <= 0 || nb <= 0) return RSDFT_OK;
     if (sym && na != nb) return fail(ctx, RSDFT_E_INVALID, "symmetric gram needs na == nb");
-    // tile edge 32 or 64 pair rows, the one with the least padding (ties: 64)
+    // Tile edge 16, 32 or 64 pair rows, the one that computes the fewest pair
+    // products (padding, and for sym the full diagonal tiles); ties: the larger.
+    // The kernel is bound by the FP64 pipe alone, so the smaller tiles' extra
+    // shared-memory loads cost nothing.
     const int pa = pairs_of(A.cnt[0]) + pairs_of(A.cnt[1]) + pairs_of(A.cnt[2]);
     const int pb = pairs_of(B.cnt[0]) + pairs_of(B.cnt[1]) + pairs_of(B.cnt[2]);
-    const long long pad2 = (long long)cdiv(pa, 32) * 32 * cdiv(pb, 32) * 32;
-    const long long pad4 = (long long)cdiv(pa, 64) * 64 * cdiv(pb, 64) * 64;
-    if (pad2 < pad4) return gram_pair_launch<2>(ctx, A, B, na, nb, g, ldg, sym, scale, st);
-    return gram_pair_launch<4>(ctx, A, B, na, nb, g, ldg, sym, scale, st);
+    auto work = [&](long long te) {
+        const long long ti = (pa + te - 1) / te, tj = (pb + te - 1) / te;
+        return (sym ? ti * (ti + 1) / 2 : ti * tj) * te * te;
+    };
+    const long long w1 = work(16), w2 = work(32), w4 = work(64);
+    if (w4 <= w2 && w4 <= w1) return gram_pair_launch<4>(ctx, A, B, na, nb, g, ldg, sym, scale, st);
+    if (w2 <= w1) return gram_pair_launch<2>(ctx, A, B, na, nb, g, ldg, sym, scale, st);
+    return gram_pair_launch<1>(ctx, A, B, na, nb, g, ldg, sym, scale, st);
 }
 
 // ---- Ritz rotation on pair rows ---------------------------------------------------------

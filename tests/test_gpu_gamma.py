@@ -45,7 +45,9 @@ def _ctx(N=(20, 18, 15), L=(5.0, 5.0, 5.0)):
     return R.Context(L, N, np.zeros(N[0] * N[1] * N[2]))
 
 
-@pytest.mark.parametrize("na,nb", [(1, 1), (7, 5), (64, 64), (67, 130), (129, 3)])
+# tiles of 16 pair rows for most shapes; 32 for (64, 64) and 64 for (256, 256),
+# where the computed work ties
+@pytest.mark.parametrize("na,nb", [(1, 1), (7, 5), (64, 64), (67, 130), (129, 3), (256, 256)])
 def test_gram_real_matches_oracle(na, nb):
     ctx = _ctx()
     a, b = draw_x0_real(1, na, ctx.n), draw_x0_real(2, nb, ctx.n)
