@@ -330,6 +330,33 @@ def time_form(ctx, R, torch, x0, wl, precision, args, barrier, stream):
             "eig0": eig0, "total_ms": total_ms, "launches": launches, "kern": kern, "outs": outs}
 
 
+def time_form_gamma(ctx, R, torch, wl, args, barrier, stream):
+    """The real Gamma-point form's SCF step (FP64, real orbitals) on the same cell
+    from a real start: the first (converged) step, warm-up, then the timed steps,
+    as time_form does for the complex forms."""
+    opts = ctx.scf_opts(n_electrons=wl.n_electrons, kT=wl.kT, beta=0.3, depth=4, k_lobpcg=3,
+                        first_maxit=200, tol=1e-6, precision=R.FP64)
+    x = torch.from_numpy(wl.x0_real()).cuda()
+    ctx.scf_init(wl.nband, opts)
+    barrier()
+    t0 = time.perf_counter()
+    out0, eig0, _ = ctx.scf_step_real(x, opts)
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        ctx.scf_step_real(x, opts)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.scf_step_real(x, opts)
+    e1.record(stream)
+    barrier()
+    return {"s_per_scf_step": e0.elapsed_time(e1) / args.steps / 1e3, "lobpcg_time_to_1e-6_s": t_first,
+            "first_step_iterations": out0.lobpcg_iterations, "eig0": eig0}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -373,6 +400,14 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
+    # ---- the real Gamma-point form's SCF step (FP64), after the e2e loop: its
+    # scf_init resets the context's SCF state; a failure here leaves the line intact
+    gamma = None
+    if args.precision == "all" and not args.no_gamma:
+        try:
+            gamma = time_form_gamma(ctx, R, torch, wl, args, barrier, stream)
+        except Exception as exc:
+            gamma = {"error": f"{type(exc).__name__}: {exc}"}
     # ---- max over ranks
     vals = reduce_max([res[f]["total_ms"] for f in forms] + [e2e_ms], dist, "cuda")
     for f, v in zip(forms, vals):
@@ -408,6 +443,9 @@ def run_ours(args, rank, world, local_rank):
             # the FP64 oracle's (converged to 1e-9 Ha from the same start)
             summary[f]["first_step_occupied_eig_max_abs_err_vs_oracle"] = float(
                 np.max(np.abs(res[f]["eig0"][:nocc] - eig_ref[:nocc])))
+        if gamma is not None and "eig0" in gamma:
+            gamma["first_step_occupied_eig_max_abs_err_vs_oracle"] = float(
+                np.max(np.abs(gamma["eig0"][:nocc] - eig_ref[:nocc])))
     # dominant kernel of the headline form by measured time ("dense" is not a
     # kernel but the group of the dense-core parts, which are listed one by one)
     hk = {k: v for k, v in summary[head]["kernels"].items() if k != "dense"}
@@ -451,6 +489,9 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": int(x.numel() * 16 + 2 * wl.nband * 8 + 88)},
             "gpu_launches": int(r["launches"]),
             "roofline": roofline, "forms": summary, "clocks": clocks}
+    if gamma is not None:
+        gamma.pop("eig0", None)
+        line["by_form"]["fp64_real_gamma"] = gamma
     if world == 1 and not args.no_cpu_baseline:
         dt = oracle_step_seconds(wl)
         line["cpu_baseline"] = {"value": dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -1104,6 +1145,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gamma", action="store_true",
+                    help="scf: skip the real Gamma-point form's SCF-step line in by_form")
     ap.add_argument("--precision", default="all", choices=["all", "fp64", "mixed", "mixed_tc"])
     ap.add_argument("--config", default="scf", choices=["scf", "batched", "learned", "micro", "large", "gamma"],
                     help="scf: the SCF-step line (default); batched: the uneven-cells batch line; "
