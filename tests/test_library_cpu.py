@@ -72,6 +72,12 @@ def test_null_arguments_rejected(lib):
     assert lib.rsdft_apply_h(None, None, None, 1, 0, None) == R.E_INVALID
     assert lib.rsdft_lobpcg(None, None, 4, None, None, None, None, None) == R.E_INVALID
     assert lib.rsdft_launch_count(None) == 0
+    # the real Gamma-point form's entry points
+    assert lib.rsdft_apply_h_real(None, None, None, 1, None) == R.E_INVALID
+    assert lib.rsdft_gram_real(None, None, 1, None, 1, None, None) == R.E_INVALID
+    assert lib.rsdft_rotate_real(None, None, 1, None, 1, None, 1, None, None) == R.E_INVALID
+    assert lib.rsdft_lobpcg_real(None, None, 4, None, None, None, None, None) == R.E_INVALID
+    assert lib.rsdft_scf_step_real(None, None, 4, None, None, None, None, None) == R.E_INVALID
 
 
 def test_create_without_gpu_reports_cuda_error(lib):
