@@ -141,3 +141,14 @@ def test_gamma_lobpcg_matches_complex_lobpcg_diamond8_24(m):
     assert rr.converged and rc.converged
     # residual 1e-8 bounds each eigenvalue error by ~res^2 / gap
     assert np.allclose(rr.eig, rc.eig, atol=1e-10, rtol=0)
+
+
+def test_gamma_lobpcg_without_preconditioner_brute_force_12cubed():
+    wl = small_cell(N=(12, 12, 12), L=(6.0, 6.0, 6.0), natom=2, nband=5)
+    ham = _cell_ham(wl)
+    g, P = ham.grid, ham.proj
+    ref = np.linalg.eigvalsh(hamiltonian_dense(g.N, g.L, ham.v, P.B.toarray(), P.E).real)
+    assert ref[5] - ref[4] > 1e-4
+    res = lobpcg_gamma(ham, draw_x0_real(wl.seed, 5, g.n), maxit=1000, tol=1e-8, precond="none")
+    assert res.converged
+    assert np.allclose(res.eig, ref[:5], atol=1e-10, rtol=0)
