@@ -224,3 +224,32 @@ def test_scf_step_real_rejects_mixed_precision():
     with pytest.raises(R.RsdftError) as e:
         ctx.scf_step_real(dev(wl.x0_real()), opts)
     assert e.value.status == R.E_INVALID
+
+
+def test_real_form_empty_and_degenerate_blocks():
+    """Empty blocks are no-ops; a rotation with no input rows leaves base (or
+    zeros); one band runs the iteration on a single padded pair row."""
+    ctx = _ctx()
+    n = ctx.n
+    empty = _real((0, n))
+    ctx.apply_h_real(empty, _real((0, n)))
+    ctx.gram_real(empty, dev(draw_x0_real(8, 3, n)), _real((0, 3)))
+    base = draw_x0_real(9, 5, n)
+    out = _real((5, n))
+    ctx.rotate_real(empty, _real((0, 5)), out, base=dev(base), sign=-1)
+    assert np.array_equal(host(out), base)
+    out.fill_(1.0)
+    ctx.rotate_real(empty, _real((0, 5)), out)
+    assert np.all(host(out) == 0.0)
+
+
+def test_lobpcg_real_one_band_matches_oracle():
+    wl = diamond8_24()
+    ctx, ham, _ = pair(wl)
+    x0 = wl.x0_real(1)
+    x = dev(x0)
+    eig, res, stats, st = ctx.lobpcg_real(x, ctx.lobpcg_opts(maxit=10, tol=0.0))
+    o = lobpcg_gamma(ham, x0, maxit=10, tol=0.0)
+    assert stats.iterations == o.iterations == 10
+    assert abs(eig[0] - o.eig[0]) < 1e-9
+    assert abs(res[0] - o.resnorm[0]) < 1e-7
